@@ -1,0 +1,315 @@
+/*
+ * aw.h - C ABI of libaw, GB300 (sm_103a) full-polarisation AW-projection
+ * gridding and degridding after arXiv:2206.15117 (Skipper, Scaife & Leahy,
+ * "A GPU-based Imager with Polarised Primary-beam Correction").
+ *
+ * General rules
+ *   - Every function returns an int status: AW_OK (0) or one of the AW_E*
+ *     codes below.  aw_last_error() returns a message for the calling thread.
+ *     No C++ exception crosses this boundary.
+ *   - Pointers marked "device" are CUDA device pointers on the context's
+ *     device; they are owned by the caller (for instance torch tensors) and
+ *     must stay valid until the work enqueued on `stream` has finished.
+ *     Pointers marked "host" are read before the call returns.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued asynchronously unless stated.
+ *   - Opaque handles (aw_ctx, aw_kernel_set, aw_plan, aw_surrogate) are
+ *     owned by the library and freed by the matching *_destroy call.
+ *
+ * Conventions (shared by every call)
+ *   - Grid of N x N uv cells (N a power of two, 16..16384), image cell dl
+ *     radians, field F = N dl, uv cell 1/F wavelengths.  Grid index g holds
+ *     u = (g - N/2)/F; image pixel q holds l = (q - N/2) dl.  Planes are
+ *     stored [npol][N][N], row (v) major, complex64 interleaved (re, im).
+ *   - npol = 1: Stokes I, no A term.  npol = 4: visibilities carry the linear
+ *     correlations XX, XY, YX, YY; grids and images carry Stokes I, Q, U, V
+ *     (Eq. 4 of the paper, with U = (XY + YX)/2).
+ *   - Degridding is V = sum I exp(-2 pi i (u l + v m + w (n - 1))) (Eq. 2 with
+ *     the usual sign); gridding is its adjoint.
+ *   - A visibility with w < 0 is handled at (-u, -v, -w) as P conj(V)
+ *     (P swaps XY and YX), exact for baseline-averaged beams (Sec. 3.2).
+ */
+#ifndef AW_H
+#define AW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define AW_OK 0
+#define AW_EINVAL 1          /* bad argument (null pointer, size, mode)          */
+#define AW_ENOMEM 2          /* device or host allocation failed                  */
+#define AW_ECUDA 3           /* a CUDA or cuFFT call failed                       */
+#define AW_ETIMEOUT 4        /* a bounded device wait gave up                     */
+#define AW_EUNSUPPORTED 5    /* valid request this build does not handle          */
+#define AW_EREJECTED 6       /* informational: surrogate bins fell back to exact  */
+
+#define AW_ROLE_GRID 0       /* uv transform of psi W ((M^S)'^-1 T): corr -> Stokes */
+#define AW_ROLE_DEGRID 1     /* uv transform of psi W* (M T^-1): Stokes -> corr     */
+#define AW_ROLE_ADJOINT 2    /* conjugate transpose of the GRID role               */
+
+#define AW_STORAGE_FP32 0    /* complex64 tables                                  */
+#define AW_STORAGE_BF16 1    /* complex as two bfloat16, FP32 arithmetic          */
+#define AW_STORAGE_FP16 2    /* complex as two float16, FP32 arithmetic           */
+
+typedef struct aw_ctx aw_ctx;
+typedef struct aw_kernel_set aw_kernel_set;
+typedef struct aw_plan aw_plan;
+typedef struct aw_surrogate aw_surrogate;
+
+/* ---- kernel specification ---------------------------------------------- */
+/*
+ * Bins: w plane p (nw planes linear in |w|, centres (p + 1/2) w_max / nw;
+ * nw = 1 switches the w term off), parallactic-angle bin a, beam-frequency
+ * bin f; bin index (p * npa + a) * nfb + f.  Sec. 3.2 of the paper averages
+ * beams over channel ranges ("for performance reasons"); these bins are that
+ * averaging.
+ */
+typedef struct aw_kernel_spec {
+    int32_t N;               /* grid side                                        */
+    double dl;               /* image cell, radians                              */
+    int32_t OS;              /* oversampling, 1..64; even if a support is odd    */
+    double W;                /* PSWF taper support in cells (c = pi W / 2)       */
+    int32_t npol;            /* 1 or 4                                           */
+    int32_t nw;              /* number of w planes, >= 1                         */
+    double w_max;            /* |w| covered by the planes, wavelengths           */
+    const int32_t *supports; /* host [nw]: full kernel width S_p per plane, 2..128 */
+    int32_t npa;             /* parallactic-angle bins (npol 4), >= 1            */
+    const double *pa;        /* host [npa]: bin centres, radians                 */
+    int32_t nfb;             /* beam-frequency bins (npol 4), >= 1               */
+    const double *fbin_freqs;/* host [nfb]: bin centres, Hz                      */
+    double dish_d;           /* dish diameter for the Airy beam, metres          */
+    double d_xy[2];          /* leakage X<-Y (re, im)                            */
+    double d_yx[2];          /* leakage Y<-X (re, im)                            */
+    double eps;              /* Eq. 6 masking fraction (paper: typically 0.2)   */
+    int32_t role;            /* AW_ROLE_*                                        */
+    int32_t storage;         /* AW_STORAGE_*                                     */
+} aw_kernel_spec;
+
+typedef struct aw_kernel_info {
+    int64_t bytes;           /* device bytes of the tables                       */
+    int32_t nbins;
+    int32_t max_support;
+    int32_t npol;
+    int32_t role;
+    int32_t storage;
+    int32_t N;
+    int32_t OS;
+    int32_t n_rejected;      /* surrogate sets: bins that use exact tables       */
+} aw_kernel_info;
+
+/* ---- visibilities -------------------------------------------------------- */
+typedef struct aw_vis_desc {
+    int64_t nvis;
+    int64_t nrow;
+    int32_t nchan;
+    const double *uvw;          /* device f64 [nrow][3], metres                  */
+    const uint32_t *row_of_vis; /* device [nvis]                                 */
+    const uint16_t *chan_of_vis;/* device [nvis]                                 */
+    const double *freq;         /* device f64 [nchan], Hz                        */
+    const uint8_t *pa_bin;      /* device [nrow] or NULL (all 0)                 */
+    const uint8_t *fbin;        /* device [nchan] or NULL (all 0)                */
+    const uint8_t *flags;       /* device [nvis] or NULL; nonzero = flagged      */
+} aw_vis_desc;
+
+typedef struct aw_tune {
+    int32_t tile;            /* grid tile side for the visibility sort, 8..256 (power of 2) */
+    int32_t chunk;           /* max visibilities per work item, 32..2048          */
+    int32_t ctas_per_sm;     /* persistent launch: CTAs per SM, 1..8              */
+    int32_t reserved;
+} aw_tune;
+
+typedef struct aw_plan_info {
+    int64_t nvis;
+    int64_t nvalid;          /* visibilities that are gridded                     */
+    int64_t n_outside;       /* skipped: footprint not inside the grid            */
+    int64_t n_flagged;       /* skipped: flagged                                  */
+    int64_t nitems;          /* work items                                        */
+    int32_t tile;
+    int32_t chunk;
+    double mean_taps;        /* mean S^2 over the valid visibilities              */
+} aw_plan_info;
+
+typedef struct aw_stats {
+    int64_t n_gridded;
+    int64_t n_outside;
+    int64_t n_flagged;
+    int64_t n_nonfinite;     /* skipped at grid time: NaN/Inf value or weight     */
+    double weight_sum;       /* sum over gridded vis of the mean correlation weight */
+} aw_stats;
+
+/* ---- context --------------------------------------------------------------- */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *aw_last_error(void);
+
+/* Create a context on CUDA device `device` (cuFFT plan cache, scratch,
+ * device status word).  *ctx receives the handle. */
+int aw_create(aw_ctx **ctx, int device);
+int aw_destroy(aw_ctx *ctx);
+
+/* ---- kernel synthesis (Sec. 3.2, Sec. 3.3, Eq. 2-6) ------------------------ */
+
+/*
+ * aw_make_kernels - build the oversampled convolution kernels of every bin.
+ *
+ * Paper: Sec. 3.2 (degridding kernels are the FFT of the Mueller-matrix cells
+ * of Eq. 5 after the anti-aliasing function and the w term; gridding kernels
+ * come from the inverse Mueller matrix) and Sec. 3.3 / Eq. 6 (the diagonal of
+ * a copy of M^S is regularised before inversion).  For every bin: the image
+ * function (taper psi(l) psi(m) x w term x Mueller cell) is sampled on M x M
+ * points over the field (M the smallest power of two >= 2 S_p, >= 16; the
+ * l = -F/2 row and column set to 0), zero-padded to (M OS)^2, transformed
+ * with a double-precision FFT, scaled by 1/M^2 and cut to S_p x S_p taps at
+ * OS x OS fine offsets.  Table layout per bin: [OS][OS][S][S][npol*npol],
+ * Mueller index out * npol + in.  A visibility at oversampled coordinate Xi
+ * covers cells x0..x0+S-1, x0 = floor((Xi - rho)/OS), rho = (S-2) OS/2; tap j
+ * holds the kernel at j OS - rho - fx oversampled units (fx the fine offset).
+ * Mueller algebra per pixel in FP64: J = E(r) [[1, d_xy], [d_yx, 1]] R(chi),
+ * E = 2 J1(x)/x (Airy), M = J (x) conj(J), M^S = T M T^-1.
+ *
+ * Runs on `stream`; the call returns once the tables are built (it
+ * synchronises `stream`).  The set is owned by the library.
+ * Errors: AW_EINVAL for a bad spec (N not a power of two, OS out of range,
+ * odd support with odd OS, npol not 1/4, null arrays), AW_ENOMEM, AW_ECUDA.
+ */
+int aw_make_kernels(aw_ctx *ctx, const aw_kernel_spec *spec, aw_kernel_set **out, void *stream);
+
+/*
+ * aw_kernel_set_import - build a set from caller tables (for instance tables
+ * evaluated by a surrogate or computed elsewhere).  `tables` is a device
+ * complex64 array holding every bin's block in the layout above, bins
+ * consecutive; it is converted to spec->storage.  spec->role is recorded.
+ */
+int aw_kernel_set_import(aw_ctx *ctx, const aw_kernel_spec *spec, const void *tables,
+                         aw_kernel_set **out, void *stream);
+
+/* Copy bin `bin`'s table as complex64 (converted from the storage type) to
+ * device memory `dst` ([OS][OS][S][S][P] complex64). */
+int aw_kernel_set_export(const aw_kernel_set *kset, int32_t bin, void *dst, void *stream);
+int aw_kernel_set_info(const aw_kernel_set *kset, aw_kernel_info *info);
+int aw_kernel_set_destroy(aw_kernel_set *kset);
+
+/* ---- plan: coordinates (FP64) and device key sort --------------------------- */
+
+/*
+ * aw_plan_create - per-visibility coordinates and the sorted work list.
+ *
+ * Paper: the baseline of Eq. 2 is in wavelengths; Sec. 2.1 (w-projection with
+ * a configurable number of w planes).  For each visibility, in FP64 with a
+ * fixed operation order and no fused multiply-add: f = freq/c,
+ * (u, v, w) = uvw f, flip if w < 0, X = u N dl OS + (N/2) OS, Xi = floor(X +
+ * 1/2), w plane floor(|w| nw / w_max) clamped, bin, footprint start x0 and
+ * fine offset fx as in aw_make_kernels.  A visibility is gridded only if its
+ * whole footprint lies inside the grid and it is not flagged.  The valid
+ * visibilities are sorted on the device (LSD radix sort: per-digit
+ * histogram, exclusive scan, stable scatter) by (bin, tile of tune->tile
+ * cells, position in tile) and cut into work items of at most tune->chunk.
+ * The plan depends on the kernel set only through N, OS, the bins and their
+ * supports; any set with the same geometry may be used with it.
+ * tune == NULL uses tile 32, chunk 256.  Synchronises `stream`.
+ */
+int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset,
+                   const aw_tune *tune, aw_plan **out, void *stream);
+int aw_plan_query(const aw_plan *plan, aw_plan_info *info);
+int aw_plan_destroy(aw_plan *plan);
+
+/*
+ * aw_plan_coords - the plan's integer coordinates in the caller's visibility
+ * order (device outputs, each [nvis]; any may be NULL): footprint start x0,
+ * y0, fine offsets fx, fy, bin, flip (0/1) and valid (0/1).  For checking.
+ */
+int aw_plan_coords(const aw_plan *plan, int32_t *x0, int32_t *y0, int32_t *fx, int32_t *fy,
+                   int32_t *bin, uint8_t *flip, uint8_t *valid, void *stream);
+
+/* aw_plan_order - the sorted order: perm[i] = caller index of the i-th
+ * visibility (device [nvis]; valid ones first, in key order). */
+int aw_plan_order(const aw_plan *plan, uint32_t *perm, void *stream);
+
+/* ---- gridding and degridding (the hot path) -------------------------------- */
+
+/*
+ * aw_grid - convolve visibilities onto the uv grid (Sec. 3.2 gridding stage).
+ *
+ *   G[s][y0+jy][x0+jx] += sum_c K[bin][fy][fx][jy][jx][s npol + c] w'_c V'_c
+ *
+ * vis: device complex64 [nvis][npol] in the caller's order; weight: device
+ * float [nvis][npol] or NULL (all 1); grid: device complex64 [npol][N][N],
+ * ACCUMULATED into (the caller zeroes it).  Visibilities with a NaN/Inf value
+ * or weight are skipped and counted.  FP32 products and sums; the summation
+ * order of overlapping footprints is not fixed (atomics).  kset must have
+ * role AW_ROLE_GRID (or any role, used as given).  If stats != NULL (host),
+ * the call synchronises `stream` and fills it.
+ */
+int aw_grid(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const void *vis,
+            const float *weight, void *grid, aw_stats *stats, void *stream);
+
+/*
+ * aw_degrid - gather a model grid into visibilities (Sec. 3.2 degridding).
+ *
+ *   V'_c = sum_s sum_taps K[bin][fy][fx][jy][jx][c npol + s] G[s][y0+jy][x0+jx]
+ *
+ * then V = P conj(V') for flipped visibilities.  grid: device complex64
+ * [npol][N][N]; vis_out: device complex64 [nvis][npol] in the caller's order,
+ * OVERWRITTEN (zero for visibilities the plan does not grid).  One warp per
+ * visibility; FP32 products, warp-shuffle reduction.
+ */
+int aw_degrid(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const void *grid,
+              void *vis_out, void *stream);
+
+/*
+ * aw_grid_batched - aw_grid as one persistent launch over the plan's work
+ * queue (every channel, polarisation and w plane of uneven counts in one
+ * launch), captured once in a CUDA graph and replayed.  ctas_per_sm from the
+ * plan's tune.  The graph is cached in the plan for the last (vis, weight,
+ * grid, kset) pointers; do not call it for one plan from two threads.
+ * Same result as aw_grid within FP32 summation-order rounding.
+ */
+int aw_grid_batched(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kset, const void *vis,
+                    const float *weight, void *grid, aw_stats *stats, void *stream);
+
+/*
+ * aw_autotune - time aw_grid_batched over candidate (tile, chunk,
+ * ctas_per_sm) on the given visibilities (pass a subsample to keep it short)
+ * and return the fastest in *out.  Uses a scratch grid it allocates.
+ * Synchronises `stream`.
+ */
+int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset, aw_tune *out,
+                void *stream);
+
+/* ---- uv grid -> image (Sec. 2.2: FFT on the GPU) ---------------------------- */
+
+/*
+ * aw_fft_to_image - dirty image planes from uv grid planes.
+ *
+ *   I(q) = sum_g G(g) exp(+2 pi i (g - N/2)(q - N/2)/N) / (c(qx) c(qy)) / weight_sum
+ *
+ * real part, c(q) = psi(2 l_q / F) the taper (grid correction); row/column 0
+ * are written as 0.  grid (device complex64 [npol][N][N], kset's N and npol)
+ * is used as FFT scratch and left transformed; image: device float
+ * [npol][N][N].  cuFFT (FP32 complex) plus the library's own shift and
+ * grid-correction kernels.
+ */
+int aw_fft_to_image(aw_ctx *ctx, const aw_kernel_set *kset, void *grid, double weight_sum,
+                    float *image, void *stream);
+
+/* ---- mosaic weighting (Sec. 2.2, Eq. 1) ------------------------------------- */
+
+/*
+ * mosaic_gamma - gamma(l, m) = [sqrt(sum B_i^2) / max sqrt(sum B_i^2)]_pbp x
+ * [1 / sum B_i^2]_wc (Eq. 1), set to 0 where the pbp factor is below eps.
+ * beams: device float [nfield][N][N]; gamma: device float [N][N].  Uses a
+ * context scratch word for the maximum.
+ */
+int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, float eps,
+                 float *gamma, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AW_H */

@@ -1,0 +1,326 @@
+"""Thin ctypes binding of libaw (include/aw.h) with the same function names.
+
+Argument marshalling only: torch tensors are passed as device pointers, the
+current torch CUDA stream as the cudaStream_t, and every step runs in the
+library's CUDA kernels.  Loading fails loudly when libaw.so is missing or no
+CUDA device is present; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaw.so")
+
+AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ETIMEOUT, AW_EUNSUPPORTED, AW_EREJECTED = range(7)
+AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT = 0, 1, 2
+AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
+
+c_i32, c_i64, c_dbl, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class aw_kernel_spec(ctypes.Structure):
+    _fields_ = [("N", c_i32), ("dl", c_dbl), ("OS", c_i32), ("W", c_dbl), ("npol", c_i32),
+                ("nw", c_i32), ("w_max", c_dbl), ("supports", ctypes.POINTER(c_i32)),
+                ("npa", c_i32), ("pa", ctypes.POINTER(c_dbl)), ("nfb", c_i32),
+                ("fbin_freqs", ctypes.POINTER(c_dbl)), ("dish_d", c_dbl),
+                ("d_xy", c_dbl * 2), ("d_yx", c_dbl * 2), ("eps", c_dbl), ("role", c_i32),
+                ("storage", c_i32)]
+
+
+class aw_kernel_info(ctypes.Structure):
+    _fields_ = [("bytes", c_i64), ("nbins", c_i32), ("max_support", c_i32), ("npol", c_i32),
+                ("role", c_i32), ("storage", c_i32), ("N", c_i32), ("OS", c_i32),
+                ("n_rejected", c_i32)]
+
+
+class aw_vis_desc(ctypes.Structure):
+    _fields_ = [("nvis", c_i64), ("nrow", c_i64), ("nchan", c_i32), ("uvw", c_p),
+                ("row_of_vis", c_p), ("chan_of_vis", c_p), ("freq", c_p), ("pa_bin", c_p),
+                ("fbin", c_p), ("flags", c_p)]
+
+
+class aw_tune(ctypes.Structure):
+    _fields_ = [("tile", c_i32), ("chunk", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32)]
+
+
+class aw_plan_info(ctypes.Structure):
+    _fields_ = [("nvis", c_i64), ("nvalid", c_i64), ("n_outside", c_i64), ("n_flagged", c_i64),
+                ("nitems", c_i64), ("tile", c_i32), ("chunk", c_i32), ("mean_taps", c_dbl)]
+
+
+class aw_stats(ctypes.Structure):
+    _fields_ = [("n_gridded", c_i64), ("n_outside", c_i64), ("n_flagged", c_i64),
+                ("n_nonfinite", c_i64), ("weight_sum", c_dbl)]
+
+
+# name -> (restype, argtypes); the exported C ABI
+SIGNATURES = {
+    "aw_last_error": (ctypes.c_char_p, []),
+    "aw_create": (ctypes.c_int, [ctypes.POINTER(c_p), ctypes.c_int]),
+    "aw_destroy": (ctypes.c_int, [c_p]),
+    "aw_make_kernels": (ctypes.c_int, [c_p, ctypes.POINTER(aw_kernel_spec), ctypes.POINTER(c_p), c_p]),
+    "aw_kernel_set_import": (ctypes.c_int, [c_p, ctypes.POINTER(aw_kernel_spec), c_p, ctypes.POINTER(c_p), c_p]),
+    "aw_kernel_set_export": (ctypes.c_int, [c_p, c_i32, c_p, c_p]),
+    "aw_kernel_set_info": (ctypes.c_int, [c_p, ctypes.POINTER(aw_kernel_info)]),
+    "aw_kernel_set_destroy": (ctypes.c_int, [c_p]),
+    "aw_plan_create": (ctypes.c_int, [c_p, ctypes.POINTER(aw_vis_desc), c_p, ctypes.POINTER(aw_tune),
+                                      ctypes.POINTER(c_p), c_p]),
+    "aw_plan_query": (ctypes.c_int, [c_p, ctypes.POINTER(aw_plan_info)]),
+    "aw_plan_destroy": (ctypes.c_int, [c_p]),
+    "aw_plan_coords": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "aw_plan_order": (ctypes.c_int, [c_p, c_p, c_p]),
+    "aw_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, ctypes.POINTER(aw_stats), c_p]),
+    "aw_degrid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p]),
+    "aw_grid_batched": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, ctypes.POINTER(aw_stats), c_p]),
+    "aw_autotune": (ctypes.c_int, [c_p, ctypes.POINTER(aw_vis_desc), c_p, ctypes.POINTER(aw_tune), c_p]),
+    "aw_fft_to_image": (ctypes.c_int, [c_p, c_p, c_p, c_dbl, c_p, c_p]),
+    "mosaic_gamma": (ctypes.c_int, [c_p, c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libaw.so and declare every exported function (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libaw.so is not built (%s): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class AWError(RuntimeError):
+    def __init__(self, code: int, fn: str, msg: str):
+        super().__init__("%s failed with status %d: %s" % (fn, code, msg))
+        self.code = code
+
+
+def _check(rc: int, fn: str):
+    if rc != AW_OK:
+        raise AWError(rc, fn, (load().aw_last_error() or b"").decode())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        return c_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return c_p(stream)
+    return c_p(stream.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _require_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libaw needs a CUDA device; none is available")
+
+
+# ---------------------------------------------------------------- context
+class Handle:
+    """Owns a library handle; keeps the tensors it refers to alive."""
+
+    def __init__(self, ptr, destroy: str, keep=()):
+        self.ptr = ptr
+        self._destroy = destroy
+        self._keep = list(keep)
+
+    def close(self):
+        if self.ptr:
+            getattr(load(), self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def aw_create(device: int = 0) -> Handle:
+    _require_cuda()
+    out = c_p()
+    _check(load().aw_create(ctypes.byref(out), device), "aw_create")
+    return Handle(out, "aw_destroy")
+
+
+def aw_destroy(ctx: Handle):
+    ctx.close()
+
+
+def make_spec(N: int, dl: float, OS: int, W: float = 7.0, npol: int = 1, nw: int = 1,
+              w_max: float = 0.0, supports: Sequence[int] = (7,), pa: Sequence[float] = (0.0,),
+              fbin_freqs: Sequence[float] = (1.4e9,), dish_d: float = 12.0, d_xy: complex = 0j,
+              d_yx: complex = 0j, eps: float = 0.2, role: int = AW_ROLE_GRID,
+              storage: int = AW_STORAGE_FP32):
+    """Build an aw_kernel_spec (returns (spec, keepalive))."""
+    sup = (c_i32 * len(supports))(*[int(s) for s in supports])
+    pa_arr = (c_dbl * len(pa))(*[float(x) for x in pa])
+    fb_arr = (c_dbl * len(fbin_freqs))(*[float(x) for x in fbin_freqs])
+    s = aw_kernel_spec()
+    s.N, s.dl, s.OS, s.W, s.npol, s.nw, s.w_max = int(N), float(dl), int(OS), float(W), int(npol), int(nw), float(w_max)
+    s.supports = ctypes.cast(sup, ctypes.POINTER(c_i32))
+    s.npa = len(pa)
+    s.pa = ctypes.cast(pa_arr, ctypes.POINTER(c_dbl))
+    s.nfb = len(fbin_freqs)
+    s.fbin_freqs = ctypes.cast(fb_arr, ctypes.POINTER(c_dbl))
+    s.dish_d = float(dish_d)
+    s.d_xy[0], s.d_xy[1] = complex(d_xy).real, complex(d_xy).imag
+    s.d_yx[0], s.d_yx[1] = complex(d_yx).real, complex(d_yx).imag
+    s.eps, s.role, s.storage = float(eps), int(role), int(storage)
+    return s, (sup, pa_arr, fb_arr)
+
+
+def aw_make_kernels(ctx: Handle, stream=None, **spec_kw) -> Handle:
+    spec, keep = make_spec(**spec_kw)
+    out = c_p()
+    _check(load().aw_make_kernels(ctx.ptr, ctypes.byref(spec), ctypes.byref(out), _stream(stream)),
+           "aw_make_kernels")
+    return Handle(out, "aw_kernel_set_destroy")
+
+
+def aw_kernel_set_import(ctx: Handle, tables, stream=None, **spec_kw) -> Handle:
+    """tables: CUDA complex64 tensor holding all bins' blocks consecutively."""
+    spec, keep = make_spec(**spec_kw)
+    out = c_p()
+    _check(load().aw_kernel_set_import(ctx.ptr, ctypes.byref(spec), _ptr(tables), ctypes.byref(out),
+                                       _stream(stream)), "aw_kernel_set_import")
+    return Handle(out, "aw_kernel_set_destroy")
+
+
+def aw_kernel_set_info(kset: Handle) -> aw_kernel_info:
+    info = aw_kernel_info()
+    _check(load().aw_kernel_set_info(kset.ptr, ctypes.byref(info)), "aw_kernel_set_info")
+    return info
+
+
+def aw_kernel_set_export(kset: Handle, b: int, dst, stream=None):
+    _check(load().aw_kernel_set_export(kset.ptr, int(b), _ptr(dst), _stream(stream)), "aw_kernel_set_export")
+
+
+def aw_kernel_set_destroy(kset: Handle):
+    kset.close()
+
+
+def vis_desc(uvw, row_of_vis, chan_of_vis, freq, pa_bin=None, fbin=None, flags=None) -> aw_vis_desc:
+    d = aw_vis_desc()
+    d.nvis = int(row_of_vis.numel())
+    d.nrow = int(uvw.shape[0])
+    d.nchan = int(freq.numel())
+    d.uvw, d.row_of_vis, d.chan_of_vis, d.freq = _ptr(uvw), _ptr(row_of_vis), _ptr(chan_of_vis), _ptr(freq)
+    d.pa_bin, d.fbin, d.flags = _ptr(pa_bin), _ptr(fbin), _ptr(flags)
+    d._keep = (uvw, row_of_vis, chan_of_vis, freq, pa_bin, fbin, flags)
+    return d
+
+
+def aw_plan_create(ctx: Handle, vis: aw_vis_desc, kset: Handle, tune: Optional[aw_tune] = None,
+                   stream=None) -> Handle:
+    out = c_p()
+    _check(load().aw_plan_create(ctx.ptr, ctypes.byref(vis), kset.ptr,
+                                 ctypes.byref(tune) if tune is not None else None, ctypes.byref(out),
+                                 _stream(stream)), "aw_plan_create")
+    return Handle(out, "aw_plan_destroy", keep=[vis, getattr(vis, "_keep", None)])
+
+
+def aw_plan_query(plan: Handle) -> aw_plan_info:
+    info = aw_plan_info()
+    _check(load().aw_plan_query(plan.ptr, ctypes.byref(info)), "aw_plan_query")
+    return info
+
+
+def aw_plan_destroy(plan: Handle):
+    plan.close()
+
+
+def aw_plan_coords(plan: Handle, x0=None, y0=None, fx=None, fy=None, bin=None, flip=None, valid=None,
+                   stream=None):
+    _check(load().aw_plan_coords(plan.ptr, _ptr(x0), _ptr(y0), _ptr(fx), _ptr(fy), _ptr(bin), _ptr(flip),
+                                 _ptr(valid), _stream(stream)), "aw_plan_coords")
+
+
+def aw_plan_order(plan: Handle, perm, stream=None):
+    _check(load().aw_plan_order(plan.ptr, _ptr(perm), _stream(stream)), "aw_plan_order")
+
+
+def aw_grid(ctx: Handle, plan: Handle, kset: Handle, vis, weight, grid, want_stats: bool = False,
+            stream=None) -> Optional[aw_stats]:
+    st = aw_stats() if want_stats else None
+    _check(load().aw_grid(ctx.ptr, plan.ptr, kset.ptr, _ptr(vis), _ptr(weight), _ptr(grid),
+                          ctypes.byref(st) if st is not None else None, _stream(stream)), "aw_grid")
+    return st
+
+
+def aw_grid_batched(ctx: Handle, plan: Handle, kset: Handle, vis, weight, grid, want_stats: bool = False,
+                    stream=None) -> Optional[aw_stats]:
+    st = aw_stats() if want_stats else None
+    _check(load().aw_grid_batched(ctx.ptr, plan.ptr, kset.ptr, _ptr(vis), _ptr(weight), _ptr(grid),
+                                  ctypes.byref(st) if st is not None else None, _stream(stream)),
+           "aw_grid_batched")
+    return st
+
+
+def aw_degrid(ctx: Handle, plan: Handle, kset: Handle, grid, vis_out, stream=None):
+    _check(load().aw_degrid(ctx.ptr, plan.ptr, kset.ptr, _ptr(grid), _ptr(vis_out), _stream(stream)),
+           "aw_degrid")
+
+
+def aw_autotune(ctx: Handle, vis: aw_vis_desc, kset: Handle, stream=None) -> aw_tune:
+    t = aw_tune()
+    _check(load().aw_autotune(ctx.ptr, ctypes.byref(vis), kset.ptr, ctypes.byref(t), _stream(stream)),
+           "aw_autotune")
+    return t
+
+
+def aw_fft_to_image(ctx: Handle, kset: Handle, grid, weight_sum: float, image, stream=None):
+    _check(load().aw_fft_to_image(ctx.ptr, kset.ptr, _ptr(grid), float(weight_sum), _ptr(image),
+                                  _stream(stream)), "aw_fft_to_image")
+
+
+def mosaic_gamma(ctx: Handle, beams, eps: float, gamma, stream=None):
+    nfield, N = int(beams.shape[0]), int(beams.shape[-1])
+    _check(load().mosaic_gamma(ctx.ptr, _ptr(beams), nfield, N, ctypes.c_float(eps), _ptr(gamma),
+                               _stream(stream)), "mosaic_gamma")
+
+
+def device_observation(ob, device="cuda:0", flags=None):
+    """Copy a synthetic Observation's arrays to the device and describe them.
+
+    Returns (aw_vis_desc, dict of tensors).  Row and channel indices are
+    passed as int32 / int16 bit patterns of the uint32 / uint16 ABI types."""
+    import numpy as np
+    import torch
+
+    def t(a, dt):
+        return torch.as_tensor(np.ascontiguousarray(a), device=device).view(dt) if a is not None else None
+
+    tens = {
+        "uvw": torch.as_tensor(np.ascontiguousarray(ob.uvw, dtype=np.float64), device=device),
+        "row": t(ob.row_of_vis.astype(np.uint32).view(np.int32), torch.int32),
+        "chan": t(ob.chan_of_vis.astype(np.uint16).view(np.int16), torch.int16),
+        "freq": torch.as_tensor(np.ascontiguousarray(ob.freq, dtype=np.float64), device=device),
+        "pa_bin": t(ob.pa_bin.astype(np.uint8), torch.uint8),
+        "fbin": t(ob.fbin.astype(np.uint8), torch.uint8),
+        "flags": t(None if flags is None else flags.astype(np.uint8), torch.uint8),
+    }
+    d = vis_desc(tens["uvw"], tens["row"], tens["chan"], tens["freq"], tens["pa_bin"], tens["fbin"],
+                 tens["flags"])
+    return d, tens

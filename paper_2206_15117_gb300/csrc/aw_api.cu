@@ -1,0 +1,448 @@
+// C ABI entry points of libaw (declared in include/aw.h): argument checks,
+// handle management, and dispatch to the kernels of the other units.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "aw_internal.h"
+
+int aw_kernel_set_geometry(const aw_kernel_spec *spec, aw_kernel_set *ks);
+int aw_kernel_set_alloc(aw_kernel_set *ks);
+int aw_synthesise(aw_ctx *ctx, aw_kernel_set *ks, cudaStream_t s);
+int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, const aw_tune *tune,
+                  aw_plan *plan, cudaStream_t s);
+int aw_plan_coords_impl(const aw_plan *plan, const aw_kernel_set *ks, int32_t *x0, int32_t *y0,
+                        int32_t *fx, int32_t *fy, int32_t *bin, uint8_t *flip, uint8_t *valid,
+                        cudaStream_t s);
+int aw_plan_order_impl(const aw_plan *plan, uint32_t *perm, cudaStream_t s);
+int aw_fft_to_image_impl(aw_ctx *ctx, int N, int npol, double W, void *grid, double weight_sum,
+                         float *image, cudaStream_t s);
+int aw_mosaic_gamma_impl(aw_ctx *ctx, const float *beams, int nfield, int N, float eps, float *gamma,
+                         cudaStream_t s);
+
+static thread_local char g_err[1024] = "";
+
+int aw_set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define AW_GUARD_BEGIN try {
+#define AW_GUARD_END                                                   \
+    }                                                                  \
+    catch (const std::bad_alloc &) {                                   \
+        return aw_set_error(AW_ENOMEM, "host allocation failed");      \
+    }                                                                  \
+    catch (...) {                                                      \
+        return aw_set_error(AW_EINVAL, "unexpected C++ exception");    \
+    }
+
+static inline cudaStream_t S_(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static int use_device(int dev) {
+    int cur = -1;
+    AW_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != dev) AW_CUDA_TRY(cudaSetDevice(dev));
+    return AW_OK;
+}
+
+int aw_ctx_fft_plan(aw_ctx *ctx, int rank_tag, int n, int batch, cufftType type, cufftHandle *out) {
+    auto key = std::make_tuple(rank_tag, n, batch, (int)type);
+    auto it = ctx->fft_plans.find(key);
+    if (it != ctx->fft_plans.end()) { *out = it->second; return AW_OK; }
+    cufftHandle h;
+    int dims[2] = {n, n};
+    AW_CUFFT_TRY(cufftPlanMany(&h, 2, dims, nullptr, 1, n * n, nullptr, 1, n * n, type, batch));
+    ctx->fft_plans[key] = h;
+    *out = h;
+    return AW_OK;
+}
+
+extern "C" {
+
+const char *aw_last_error(void) { return g_err; }
+
+int aw_create(aw_ctx **ctx, int device) {
+    AW_GUARD_BEGIN
+    if (!ctx) return aw_set_error(AW_EINVAL, "ctx is NULL");
+    *ctx = nullptr;
+    int ndev = 0;
+    AW_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return aw_set_error(AW_EINVAL, "device %d of %d", device, ndev);
+    AW_CUDA_TRY(cudaSetDevice(device));
+    aw_ctx *c = new aw_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->d_scratch, 256);
+    if (e != cudaSuccess) {
+        delete c;
+        return aw_set_error(AW_ENOMEM, "context scratch: %s", cudaGetErrorString(e));
+    }
+    *ctx = c;
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_destroy(aw_ctx *ctx) {
+    AW_GUARD_BEGIN
+    if (!ctx) return AW_OK;
+    use_device(ctx->device);
+    for (auto &kv : ctx->fft_plans) cufftDestroy(kv.second);
+    for (auto &kv : ctx->gridcorr) cudaFree(kv.second);
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    delete ctx;
+    return AW_OK;
+    AW_GUARD_END
+}
+
+static void free_kset(aw_kernel_set *k) {
+    if (!k) return;
+    if (k->d_table) cudaFree(k->d_table);
+    if (k->d_bin_support) cudaFree(k->d_bin_support);
+    if (k->d_bin_offset) cudaFree(k->d_bin_offset);
+    delete k;
+}
+
+int aw_make_kernels(aw_ctx *ctx, const aw_kernel_spec *spec, aw_kernel_set **out, void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx || !out) return aw_set_error(AW_EINVAL, "ctx/out is NULL");
+    *out = nullptr;
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    aw_kernel_set *k = new aw_kernel_set();
+    k->device = ctx->device;
+    rc = aw_kernel_set_geometry(spec, k);
+    if (rc == AW_OK) rc = aw_kernel_set_alloc(k);
+    if (rc == AW_OK) rc = aw_synthesise(ctx, k, S_(stream));
+    if (rc != AW_OK) { free_kset(k); return rc; }
+    *out = k;
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_kernel_set_import(aw_ctx *ctx, const aw_kernel_spec *spec, const void *tables, aw_kernel_set **out,
+                         void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx || !out || !tables) return aw_set_error(AW_EINVAL, "ctx/out/tables is NULL");
+    *out = nullptr;
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    aw_kernel_set *k = new aw_kernel_set();
+    k->device = ctx->device;
+    rc = aw_kernel_set_geometry(spec, k);
+    if (rc == AW_OK) rc = aw_kernel_set_alloc(k);
+    if (rc == AW_OK && k->spec.storage == AW_STORAGE_FP16) {
+        float mx = 0.f;
+        rc = aw_table_absmax(reinterpret_cast<const float2 *>(tables), k->total_elems, &mx, S_(stream));
+        if (rc == AW_OK && mx > 0.f) k->scale = (float)std::ldexp(1.0, (int)std::floor(-std::log2((double)mx)));
+    }
+    if (rc == AW_OK)
+        rc = aw_convert_table_scaled(reinterpret_cast<const float2 *>(tables), k->d_table, k->total_elems,
+                                     k->spec.storage, k->scale, S_(stream));
+    if (rc == AW_OK) {
+        cudaError_t e = cudaStreamSynchronize(S_(stream));
+        if (e != cudaSuccess) rc = aw_set_error(AW_ECUDA, "import: %s", cudaGetErrorString(e));
+    }
+    if (rc != AW_OK) { free_kset(k); return rc; }
+    *out = k;
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_kernel_set_export(const aw_kernel_set *k, int32_t bin, void *dst, void *stream) {
+    AW_GUARD_BEGIN
+    if (!k || !dst) return aw_set_error(AW_EINVAL, "kset/dst is NULL");
+    if (bin < 0 || bin >= k->nbins) return aw_set_error(AW_EINVAL, "bin %d of %d", bin, k->nbins);
+    int rc = use_device(k->device);
+    if (rc) return rc;
+    const int S = k->bin_support[bin];
+    const int64_t n = (int64_t)k->spec.OS * k->spec.OS * S * S * k->P;
+    const char *src = static_cast<const char *>(k->d_table) + k->bin_offset[bin] * k->elem_bytes;
+    return aw_export_table(src, reinterpret_cast<float2 *>(dst), n, k->spec.storage, 1.0f / k->scale,
+                           S_(stream));
+    AW_GUARD_END
+}
+
+int aw_kernel_set_info(const aw_kernel_set *k, aw_kernel_info *info) {
+    if (!k || !info) return aw_set_error(AW_EINVAL, "kset/info is NULL");
+    info->bytes = k->total_elems * k->elem_bytes;
+    info->nbins = k->nbins;
+    info->max_support = k->max_support;
+    info->npol = k->spec.npol;
+    info->role = k->spec.role;
+    info->storage = k->spec.storage;
+    info->N = k->spec.N;
+    info->OS = k->spec.OS;
+    info->n_rejected = k->n_rejected;
+    return AW_OK;
+}
+
+int aw_kernel_set_destroy(aw_kernel_set *k) {
+    AW_GUARD_BEGIN
+    if (!k) return AW_OK;
+    use_device(k->device);
+    free_kset(k);
+    return AW_OK;
+    AW_GUARD_END
+}
+
+static void free_plan(aw_plan *p) {
+    if (!p) return;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->d_rec) cudaFree(p->d_rec);
+    if (p->d_items) cudaFree(p->d_items);
+    if (p->d_plane_support) cudaFree(p->d_plane_support);
+    if (p->d_wsum) cudaFree(p->d_wsum);
+    if (p->d_nonfinite) cudaFree(p->d_nonfinite);
+    if (p->d_counter) cudaFree(p->d_counter);
+    delete p;
+}
+
+int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset, const aw_tune *tune,
+                   aw_plan **out, void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx || !kset || !out) return aw_set_error(AW_EINVAL, "ctx/kset/out is NULL");
+    *out = nullptr;
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    aw_plan *p = new aw_plan();
+    p->device = ctx->device;
+    rc = aw_plan_build(ctx, vis, kset, tune, p, S_(stream));
+    if (rc != AW_OK) { free_plan(p); return rc; }
+    *out = p;
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_plan_query(const aw_plan *p, aw_plan_info *info) {
+    if (!p || !info) return aw_set_error(AW_EINVAL, "plan/info is NULL");
+    info->nvis = p->nvis;
+    info->nvalid = p->nvalid;
+    info->n_outside = p->n_outside;
+    info->n_flagged = p->n_flagged;
+    info->nitems = p->nitems;
+    info->tile = p->tune.tile;
+    info->chunk = p->tune.chunk;
+    info->mean_taps = p->mean_taps;
+    return AW_OK;
+}
+
+int aw_plan_destroy(aw_plan *p) {
+    AW_GUARD_BEGIN
+    if (!p) return AW_OK;
+    use_device(p->device);
+    free_plan(p);
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_plan_coords(const aw_plan *p, int32_t *x0, int32_t *y0, int32_t *fx, int32_t *fy, int32_t *bin,
+                   uint8_t *flip, uint8_t *valid, void *stream) {
+    AW_GUARD_BEGIN
+    if (!p) return aw_set_error(AW_EINVAL, "plan is NULL");
+    int rc = use_device(p->device);
+    if (rc) return rc;
+    return aw_plan_coords_impl(p, nullptr, x0, y0, fx, fy, bin, flip, valid, S_(stream));
+    AW_GUARD_END
+}
+
+int aw_plan_order(const aw_plan *p, uint32_t *perm, void *stream) {
+    AW_GUARD_BEGIN
+    if (!p || !perm) return aw_set_error(AW_EINVAL, "plan/perm is NULL");
+    int rc = use_device(p->device);
+    if (rc) return rc;
+    return aw_plan_order_impl(p, perm, S_(stream));
+    AW_GUARD_END
+}
+
+static int check_pair(const aw_plan *p, const aw_kernel_set *k) {
+    if (!p || !k) return aw_set_error(AW_EINVAL, "plan/kset is NULL");
+    if (p->N != k->spec.N || p->OS != k->spec.OS || p->npol != k->spec.npol || p->nbins != k->nbins ||
+        p->bin_support != k->bin_support)
+        return aw_set_error(AW_EINVAL, "kernel set geometry does not match the plan");
+    return AW_OK;
+}
+
+static int fill_stats(const aw_plan *p, aw_stats *stats, cudaStream_t s) {
+    double ws = 0;
+    unsigned long long nb = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&ws, p->d_wsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaMemcpyAsync(&nb, p->d_nonfinite, sizeof(nb), cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    stats->n_nonfinite = (int64_t)nb;
+    stats->n_gridded = p->nvalid - (int64_t)nb;
+    stats->n_outside = p->n_outside;
+    stats->n_flagged = p->n_flagged;
+    stats->weight_sum = ws;
+    return AW_OK;
+}
+
+int aw_grid(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k, const void *vis, const float *weight,
+            void *grid, aw_stats *stats, void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx) return aw_set_error(AW_EINVAL, "ctx is NULL");
+    int rc = check_pair(p, k);
+    if (rc) return rc;
+    if ((!vis && p->nvis) || !grid) return aw_set_error(AW_EINVAL, "vis/grid is NULL");
+    rc = use_device(ctx->device);
+    if (rc) return rc;
+    cudaStream_t s = S_(stream);
+    AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), s));
+    AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), s));
+    aw_grid_launch L{p, k, vis, weight, grid, false, 0, s};
+    rc = aw_launch_grid(L);
+    if (rc) return rc;
+    if (stats) return fill_stats(p, stats, s);
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_degrid(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k, const void *grid, void *vis_out,
+              void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx) return aw_set_error(AW_EINVAL, "ctx is NULL");
+    int rc = check_pair(p, k);
+    if (rc) return rc;
+    if (!grid || (!vis_out && p->nvis)) return aw_set_error(AW_EINVAL, "grid/vis_out is NULL");
+    rc = use_device(ctx->device);
+    if (rc) return rc;
+    return aw_launch_degrid(p, k, grid, vis_out, S_(stream));
+    AW_GUARD_END
+}
+
+int aw_grid_batched(aw_ctx *ctx, aw_plan *p, const aw_kernel_set *k, const void *vis, const float *weight,
+                    void *grid, aw_stats *stats, void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx) return aw_set_error(AW_EINVAL, "ctx is NULL");
+    int rc = check_pair(p, k);
+    if (rc) return rc;
+    if ((!vis && p->nvis) || !grid) return aw_set_error(AW_EINVAL, "vis/grid is NULL");
+    rc = use_device(ctx->device);
+    if (rc) return rc;
+    cudaStream_t s = S_(stream);
+    if (p->nitems == 0) {
+        AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), s));
+        AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), s));
+        if (stats) return fill_stats(p, stats, s);
+        return AW_OK;
+    }
+    const bool same = p->graph && p->g_vis == vis && p->g_weight == weight && p->g_grid == grid &&
+                      p->g_kset == k && p->g_stream == s;
+    if (!same) {
+        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        cudaStream_t cap;
+        AW_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        int ctas = ctx->sm_count * p->tune.ctas_per_sm;
+        if (ctas > p->nitems) ctas = (int)p->nitems;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(p->d_wsum, 0, sizeof(double), cap);
+            cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), cap);
+            cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), cap);
+            aw_grid_launch L{p, k, vis, weight, grid, true, ctas, cap};
+            rc = aw_launch_grid(L);
+            e = cudaStreamEndCapture(cap, &g);
+        }
+        if (e == cudaSuccess && rc == AW_OK) e = cudaGraphInstantiate(&p->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        if (rc) return rc;
+        if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        p->g_vis = vis;
+        p->g_weight = weight;
+        p->g_grid = grid;
+        p->g_kset = k;
+        p->g_stream = s;
+    }
+    AW_CUDA_TRY(cudaGraphLaunch(p->graph, s));
+    if (stats) return fill_stats(p, stats, s);
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_tune *out, void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx || !vis || !k || !out) return aw_set_error(AW_EINVAL, "NULL argument");
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    cudaStream_t s = S_(stream);
+    const size_t gbytes = sizeof(float2) * (size_t)k->spec.npol * k->spec.N * k->spec.N;
+    void *grid = nullptr, *v = nullptr;
+    AW_CUDA_TRY(cudaMalloc(&grid, gbytes));
+    cudaError_t e = cudaMalloc(&v, sizeof(float2) * (size_t)k->spec.npol * std::max<int64_t>(vis->nvis, 1));
+    if (e != cudaSuccess) { cudaFree(grid); return aw_set_error(AW_ENOMEM, "autotune vis buffer"); }
+    cudaMemsetAsync(v, 0, sizeof(float2) * (size_t)k->spec.npol * std::max<int64_t>(vis->nvis, 1), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int tiles[] = {16, 32, 64};
+    const int chunks[] = {128, 256, 512};
+    const int ctas[] = {1, 2, 4};
+    float best = 1e30f;
+    aw_tune bt{32, 256, 2, 0};
+    for (int t : tiles) {
+        for (int c : chunks) {
+            aw_tune tu{t, c, 1, 0};
+            aw_plan *p = new aw_plan();
+            p->device = ctx->device;
+            rc = aw_plan_build(ctx, vis, k, &tu, p, s);
+            if (rc) { free_plan(p); break; }
+            for (int cp : ctas) {
+                p->tune.ctas_per_sm = cp;
+                if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3 && rc == AW_OK; ++rep) {
+                    cudaMemsetAsync(grid, 0, gbytes, s);
+                    cudaEventRecord(e0, s);
+                    rc = aw_grid_batched(ctx, p, k, v, nullptr, grid, nullptr, stream);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < ms_best) ms_best = ms;
+                }
+                if (rc) break;
+                if (ms_best < best) { best = ms_best; bt = aw_tune{t, c, cp, 0}; }
+            }
+            free_plan(p);
+            if (rc) break;
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(grid);
+    cudaFree(v);
+    if (rc) return rc;
+    *out = bt;
+    return AW_OK;
+    AW_GUARD_END
+}
+
+int aw_fft_to_image(aw_ctx *ctx, const aw_kernel_set *k, void *grid, double weight_sum, float *image,
+                    void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx || !k || !grid || !image) return aw_set_error(AW_EINVAL, "NULL argument");
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    return aw_fft_to_image_impl(ctx, k->spec.N, k->spec.npol, k->spec.W, grid, weight_sum, image, S_(stream));
+    AW_GUARD_END
+}
+
+int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, float eps, float *gamma,
+                 void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx || !beams || !gamma) return aw_set_error(AW_EINVAL, "NULL argument");
+    if (nfield < 1 || N < 1) return aw_set_error(AW_EINVAL, "nfield=%d N=%d", nfield, N);
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    return aw_mosaic_gamma_impl(ctx, beams, nfield, N, eps, gamma, S_(stream));
+    AW_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations shared by the libaw translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "aw.h"
+
+#define AW_C_LIGHT 299792458.0
+
+// ---------------------------------------------------------------- errors
+int aw_set_error(int code, const char *fmt, ...);
+
+#define AW_CUDA_TRY(call)                                                             \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return aw_set_error(e_ == cudaErrorMemoryAllocation ? AW_ENOMEM : AW_ECUDA, \
+                                "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                                __FILE__, __LINE__);                                  \
+    } while (0)
+
+#define AW_CUFFT_TRY(call)                                                            \
+    do {                                                                              \
+        cufftResult r_ = (call);                                                      \
+        if (r_ != CUFFT_SUCCESS)                                                      \
+            return aw_set_error(r_ == CUFFT_ALLOC_FAILED ? AW_ENOMEM : AW_ECUDA,        \
+                                "%s: cufft error %d (%s:%d)", #call, (int)r_,          \
+                                __FILE__, __LINE__);                                  \
+    } while (0)
+
+#define AW_CHECK_LAUNCH() AW_CUDA_TRY(cudaGetLastError())
+
+// ---------------------------------------------------------------- handles
+struct aw_ctx {
+    int device = 0;
+    int sm_count = 0;
+    // cuFFT plans keyed by (rank tag, size, batch, type)
+    std::map<std::tuple<int, int, int, int>, cufftHandle> fft_plans;
+    // grid-correction vectors keyed by (N, W)
+    std::map<std::pair<int, double>, float *> gridcorr;
+    // small device scratch: [0] reduction word for mosaic_gamma
+    unsigned int *d_scratch = nullptr;
+};
+
+struct aw_kernel_set {
+    int device = 0;
+    aw_kernel_spec spec{};          // copied; pointer members re-pointed to the vectors
+    std::vector<int32_t> supports;  // per w plane
+    std::vector<double> pa, fbin_freqs;
+    int nbins = 0;
+    int P = 1;                      // npol * npol
+    int max_support = 0;
+    std::vector<int32_t> bin_support;
+    std::vector<int64_t> bin_offset;  // element offset of each bin (complex elements)
+    int64_t total_elems = 0;
+    int elem_bytes = 8;
+    void *d_table = nullptr;
+    int32_t *d_bin_support = nullptr;
+    int64_t *d_bin_offset = nullptr;
+    int n_rejected = 0;
+    // tables hold K * scale (a power of two; != 1 only for FP16 storage, to keep
+    // the kernel values inside the FP16 normal range)
+    float scale = 1.0f;
+};
+
+// One sorted visibility: 16 bytes.
+struct __align__(16) aw_rec {
+    uint32_t orig;   // caller index
+    uint16_t x0, y0; // first footprint cell
+    uint16_t bin;
+    uint8_t fx, fy;  // fine offsets
+    uint8_t flip;
+    uint8_t pad0;
+    uint16_t pad1;
+};
+static_assert(sizeof(aw_rec) == 16, "aw_rec must be 16 bytes");
+
+struct aw_plan {
+    int device = 0;
+    int64_t nvis = 0, nvalid = 0, n_outside = 0, n_flagged = 0, nitems = 0;
+    int N = 0, OS = 0, npol = 1, nbins = 0, nw = 1, npa = 1, nfb = 1;
+    aw_tune tune{};
+    double mean_taps = 0;
+    aw_rec *d_rec = nullptr;        // [nvis] sorted (valid first)
+    int4 *d_items = nullptr;        // [nitems] {start, count, bin, tile}
+    int32_t *d_plane_support = nullptr;  // [nw] support per w plane
+    std::vector<int32_t> bin_support;
+    // grid-time statistics (device): [0] weight sum (double), [1] non-finite count
+    double *d_wsum = nullptr;
+    unsigned long long *d_nonfinite = nullptr;
+    unsigned int *d_counter = nullptr;  // persistent work-queue head
+    // coordinate inputs kept for aw_plan_coords
+    aw_vis_desc vis{};
+    double uscale = 0, half = 0, winv = 0;
+    // cached graph for aw_grid_batched
+    cudaGraphExec_t graph = nullptr;
+    const void *g_vis = nullptr, *g_weight = nullptr, *g_grid = nullptr, *g_kset = nullptr;
+    cudaStream_t g_stream = nullptr;
+};
+
+// ---------------------------------------------------------------- helpers
+int aw_ctx_fft_plan(aw_ctx *ctx, int rank_tag, int n, int batch, cufftType type, cufftHandle *out);
+int aw_ctx_gridcorr(aw_ctx *ctx, int N, double W, float **out);
+
+// PSWF taper psi(x), psi(0) = 1, from the Legendre eigen-expansion (host).
+struct aw_pswf {
+    std::vector<double> beta;  // coefficients of Pbar_{2k}
+    double norm = 1.0;         // 1 / psi_unnormalised(0)
+    double eval(double x) const;
+};
+aw_pswf aw_pswf_make(double c, int nterms = 48);
+
+// Exclusive scan of uint32 (n up to 2^31) with caller scratch from aw_scan_scratch_bytes.
+size_t aw_scan_scratch_bytes(int64_t n);
+int aw_exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, void *scratch,
+                          cudaStream_t s);
+
+// Grid / degrid launchers (aw_grid.cu).
+struct aw_grid_launch {
+    const aw_plan *plan;
+    const aw_kernel_set *kset;
+    const void *vis;
+    const float *weight;
+    void *grid;
+    bool persistent;
+    int ctas;
+    cudaStream_t stream;
+};
+int aw_launch_grid(const aw_grid_launch &L);
+int aw_launch_degrid(const aw_plan *plan, const aw_kernel_set *kset, const void *grid,
+                     void *vis_out, cudaStream_t stream);
+
+// Storage conversion (aw_synth.cu).
+int aw_convert_table(const float2 *src, void *dst, int64_t n, int storage, cudaStream_t s);
+int aw_export_table(const void *src, float2 *dst, int64_t n, int storage, float inv_scale, cudaStream_t s);
+int aw_convert_table_scaled(const float2 *src, void *dst, int64_t n, int storage, float scale, cudaStream_t s);
+int aw_table_absmax(const float2 *src, int64_t n, float *out_host, cudaStream_t s);

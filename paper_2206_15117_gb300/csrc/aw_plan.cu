@@ -1,0 +1,586 @@
+// Plan creation: per-visibility FP64 coordinates (uvw in wavelengths, Eq. 2)
+// and the device key sort that orders visibilities by (bin, grid tile,
+// position in tile) and cuts them into work items.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "aw_internal.h"
+
+namespace {
+
+struct CoordArgs {
+    int64_t nvis;
+    const double *uvw;
+    const uint32_t *row;
+    const uint16_t *chan;
+    const double *freq;
+    const uint8_t *pa_bin;
+    const uint8_t *fbin;
+    const uint8_t *flags;
+    int N, OS, nw, npa, nfb;
+    double uscale, half, winv;
+    const int32_t *support;  // per w plane
+    int tile, tbits, ntx, nty;
+    int64_t nrow;
+    int32_t nchan;
+};
+
+struct CoordOut {
+    int x0, y0, fx, fy, bin, flip, valid, S;
+};
+
+// The FP64 coordinate step with a fixed operation order (no contraction).
+__device__ __forceinline__ CoordOut coord_of(const CoordArgs &a, int64_t k) {
+    CoordOut o;
+    const uint32_t r = a.row[k];
+    const uint16_t c = a.chan[k];
+    const double f = __ddiv_rn(a.freq[c], AW_C_LIGHT);
+    double u = __dmul_rn(a.uvw[3 * (int64_t)r + 0], f);
+    double v = __dmul_rn(a.uvw[3 * (int64_t)r + 1], f);
+    double w = __dmul_rn(a.uvw[3 * (int64_t)r + 2], f);
+    o.flip = 0;
+    if (w < 0.0) { u = -u; v = -v; w = -w; o.flip = 1; }
+    const double xr = __dadd_rn(__dadd_rn(__dmul_rn(u, a.uscale), a.half), 0.5);
+    const double yr = __dadd_rn(__dadd_rn(__dmul_rn(v, a.uscale), a.half), 0.5);
+    // clamp far-out values before the integer conversion; they are invalid anyway
+    const double lim = 4.0e15;
+    const long long Xi = (long long)floor(fmin(fmax(xr, -lim), lim));
+    const long long Yi = (long long)floor(fmin(fmax(yr, -lim), lim));
+    int wp = 0;
+    if (a.winv > 0.0) {
+        const double wt = __dmul_rn(w, a.winv);
+        const double fw = floor(fmin(wt, 1.0e9));
+        wp = (int)fw;
+        if (wp < 0) wp = 0;
+        if (wp > a.nw - 1) wp = a.nw - 1;
+    }
+    const int pa = a.pa_bin ? (int)a.pa_bin[r] : 0;
+    const int fb = a.fbin ? (int)a.fbin[c] : 0;
+    o.bin = (wp * a.npa + min(pa, a.npa - 1)) * a.nfb + min(fb, a.nfb - 1);
+    const int S = a.support[wp];
+    o.S = S;
+    const long long rho = (long long)(S - 2) * a.OS / 2;
+    const long long Ax = Xi - rho, Ay = Yi - rho;
+    long long ix = Ax / a.OS; if (Ax < 0 && ix * a.OS != Ax) ix -= 1;
+    long long iy = Ay / a.OS; if (Ay < 0 && iy * a.OS != Ay) iy -= 1;
+    o.fx = (int)(Ax - ix * a.OS);
+    o.fy = (int)(Ay - iy * a.OS);
+    int valid = 1;
+    if (ix < 0 || ix + S > a.N) valid = 0;
+    if (iy < 0 || iy + S > a.N) valid = 0;
+    o.x0 = valid ? (int)ix : 0;
+    o.y0 = valid ? (int)iy : 0;
+    o.valid = valid;
+    return o;
+}
+
+__global__ void coords_kernel(CoordArgs a, uint64_t invalid_key, uint64_t *keys, uint32_t *vals,
+                              aw_rec *recs, unsigned long long *counts /* outside, flagged, valid, taps */) {
+    unsigned long long n_out = 0, n_flag = 0, n_val = 0, taps = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.nvis;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const CoordOut o = coord_of(a, k);
+        const bool flagged = a.flags && a.flags[k];
+        const bool ok = o.valid && !flagged;
+        if (!o.valid) n_out++;
+        else if (flagged) n_flag++;
+        uint64_t key = invalid_key;
+        if (ok) {
+            n_val++;
+            taps += (unsigned long long)o.S * o.S;
+            const int tx = o.x0 >> a.tbits, ty = o.y0 >> a.tbits;
+            const int lx = o.x0 & (a.tile - 1), ly = o.y0 & (a.tile - 1);
+            key = ((((uint64_t)o.bin * a.nty + ty) * a.ntx + tx) << (2 * a.tbits)) |
+                  ((uint64_t)ly << a.tbits) | (uint64_t)lx;
+        }
+        keys[k] = key;
+        vals[k] = (uint32_t)k;
+        aw_rec rc;
+        rc.orig = (uint32_t)k;
+        rc.x0 = (uint16_t)o.x0;
+        rc.y0 = (uint16_t)o.y0;
+        rc.bin = (uint16_t)o.bin;
+        rc.fx = (uint8_t)o.fx;
+        rc.fy = (uint8_t)o.fy;
+        rc.flip = (uint8_t)o.flip;
+        rc.pad0 = 0;
+        rc.pad1 = 0;
+        recs[k] = rc;
+    }
+    // warp-aggregated counters
+    for (int off = 16; off; off >>= 1) {
+        n_out += __shfl_xor_sync(0xffffffffu, n_out, off);
+        n_flag += __shfl_xor_sync(0xffffffffu, n_flag, off);
+        n_val += __shfl_xor_sync(0xffffffffu, n_val, off);
+        taps += __shfl_xor_sync(0xffffffffu, taps, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_out) atomicAdd(&counts[0], n_out);
+        if (n_flag) atomicAdd(&counts[1], n_flag);
+        if (n_val) atomicAdd(&counts[2], n_val);
+        if (taps) atomicAdd(&counts[3], taps);
+    }
+}
+
+__global__ void coords_out_kernel(CoordArgs a, int32_t *x0, int32_t *y0, int32_t *fx, int32_t *fy,
+                                  int32_t *bin, uint8_t *flip, uint8_t *valid) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.nvis;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const CoordOut o = coord_of(a, k);
+        const bool ok = o.valid && !(a.flags && a.flags[k]);
+        if (x0) x0[k] = o.x0;
+        if (y0) y0[k] = o.y0;
+        if (fx) fx[k] = o.fx;
+        if (fy) fy[k] = o.fy;
+        if (bin) bin[k] = o.bin;
+        if (flip) flip[k] = (uint8_t)o.flip;
+        if (valid) valid[k] = ok ? 1 : 0;
+    }
+}
+
+// ------------------------------------------------------------ LSD radix sort
+// One pass = per-tile digit histogram -> exclusive scan over [digit][tile] ->
+// stable scatter.  A tile is RS_THREADS * RS_ITEMS keys; each warp owns a
+// contiguous run of RS_ITEMS * 32 keys, ranks equal digits with
+// __match_any_sync, and keeps its own running digit counters, so the order of
+// equal keys is preserved.
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__global__ void radix_hist_kernel(const uint64_t *keys, int64_t n, int shift, uint32_t *counts,
+                                  int ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = 0; i < RS_ITEMS; ++i) {
+        const int64_t k = base + (int64_t)i * RS_THREADS + threadIdx.x;
+        if (k < n) atomicAdd(&h[(keys[k] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void radix_scatter_kernel(const uint64_t *keys, const uint32_t *vals, int64_t n, int shift,
+                                     const uint32_t *offsets, int ntiles, uint64_t *keys_out,
+                                     uint32_t *vals_out) {
+    __shared__ uint32_t wbase[RS_WARPS][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wbase[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t wstart = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * RS_ITEMS * 32;
+    uint64_t kk[RS_ITEMS];
+    uint32_t vv[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t k = wstart + r * 32 + lane;
+        kk[r] = (k < n) ? keys[k] : 0;
+        vv[r] = (k < n) ? vals[k] : 0;
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    // 1) per-warp digit counts
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t k = wstart + r * 32 + lane;
+        const unsigned act = __ballot_sync(0xffffffffu, k < n);
+        if (k < n) {
+            const unsigned d = (unsigned)((kk[r] >> shift) & 0xFF);
+            const unsigned peers = __match_any_sync(act, d);
+            if ((peers & lt) == 0) wbase[warp][d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // 2) warp bases: global tile offset + counts of the earlier warps
+    {
+        const int d = threadIdx.x;  // RS_THREADS == 256 digits
+        uint32_t run = offsets[(int64_t)d * ntiles + blockIdx.x];
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const uint32_t c = wbase[w][d];
+            wbase[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // 3) stable scatter, rounds in order
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t k = wstart + r * 32 + lane;
+        const unsigned act = __ballot_sync(0xffffffffu, k < n);
+        unsigned d = 0, peers = 0;
+        uint32_t pos = 0;
+        if (k < n) {
+            d = (unsigned)((kk[r] >> shift) & 0xFF);
+            peers = __match_any_sync(act, d);
+            pos = wbase[warp][d] + __popc(peers & lt);
+            keys_out[pos] = kk[r];
+            vals_out[pos] = vv[r];
+        }
+        __syncwarp();
+        if (k < n && (peers & lt) == 0) wbase[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------ items
+__global__ void seg_flag_kernel(const uint64_t *keys, int64_t nvalid, int tb2, uint32_t *flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvalid;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = (i == 0 || (keys[i] >> tb2) != (keys[i - 1] >> tb2)) ? 1u : 0u;
+}
+
+__global__ void seg_start_kernel(const uint32_t *flag, const uint32_t *segid, int64_t nvalid,
+                                 uint32_t *starts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvalid;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) starts[segid[i]] = (uint32_t)i;
+}
+
+__global__ void seg_chunks_kernel(const uint32_t *starts, int64_t nseg, uint32_t nvalid, int chunk,
+                                  uint32_t *nch) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = starts[s];
+        const uint32_t b = (s + 1 < nseg) ? starts[s + 1] : nvalid;
+        nch[s] = (b - a + chunk - 1) / chunk;
+    }
+}
+
+__global__ void emit_items_kernel(const uint32_t *starts, const uint32_t *itembase, int64_t nseg,
+                                  uint32_t nvalid, int chunk, const aw_rec *rec, int4 *items) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = starts[s];
+        const uint32_t b = (s + 1 < nseg) ? starts[s + 1] : nvalid;
+        const int bin = rec[a].bin;
+        uint32_t pos = itembase[s];
+        for (uint32_t st = a; st < b; st += chunk) {
+            const uint32_t cnt = min((uint32_t)chunk, b - st);
+            items[pos++] = make_int4((int)st, (int)cnt, bin, 0);
+        }
+    }
+}
+
+__global__ void gather_rec_kernel(const aw_rec *in, const uint32_t *perm, int64_t n, aw_rec *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+__global__ void rec_orig_kernel(const aw_rec *rec, int64_t n, uint32_t *perm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        perm[i] = rec[i].orig;
+}
+
+int grid_blocks(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+int fill_coord_args(const aw_vis_desc *vis, const aw_kernel_set *ks, int tile, CoordArgs &a,
+                    aw_plan *plan) {
+    const aw_kernel_spec &sp = ks->spec;
+    a.nvis = vis->nvis;
+    a.uvw = vis->uvw;
+    a.row = vis->row_of_vis;
+    a.chan = vis->chan_of_vis;
+    a.freq = vis->freq;
+    a.pa_bin = vis->pa_bin;
+    a.fbin = vis->fbin;
+    a.flags = vis->flags;
+    a.N = sp.N;
+    a.OS = sp.OS;
+    a.nw = sp.nw;
+    a.npa = sp.npa;
+    a.nfb = sp.nfb;
+    a.uscale = (double)sp.N * sp.dl * (double)sp.OS;
+    a.half = (double)(sp.N / 2) * (double)sp.OS;
+    a.winv = (sp.nw > 1 && sp.w_max > 0.0) ? (double)sp.nw / sp.w_max : 0.0;
+    a.support = plan->d_plane_support;  // first nw entries hold the per-plane supports
+    a.tile = tile;
+    a.tbits = ilog2(tile);
+    a.ntx = (sp.N + tile - 1) / tile;
+    a.nty = a.ntx;
+    a.nrow = vis->nrow;
+    a.nchan = vis->nchan;
+    return AW_OK;
+}
+
+}  // namespace
+
+int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, const aw_tune *tune,
+                  aw_plan *plan, cudaStream_t s) {
+    (void)ctx;
+    if (!vis || vis->nvis < 0 || (vis->nvis > 0 && (!vis->uvw || !vis->row_of_vis || !vis->chan_of_vis || !vis->freq)))
+        return aw_set_error(AW_EINVAL, "vis descriptor incomplete");
+    if (vis->nvis > 0x7fffffffLL) return aw_set_error(AW_EINVAL, "nvis %lld above 2^31-1", (long long)vis->nvis);
+    const aw_kernel_spec &sp = ks->spec;
+    aw_tune t = tune ? *tune : aw_tune{32, 256, 2, 0};
+    if (t.tile < 8 || t.tile > 256 || (t.tile & (t.tile - 1))) return aw_set_error(AW_EINVAL, "tile %d", t.tile);
+    if (t.chunk < 32 || t.chunk > 2048) return aw_set_error(AW_EINVAL, "chunk %d", t.chunk);
+    if (t.ctas_per_sm < 1 || t.ctas_per_sm > 8) t.ctas_per_sm = 2;
+    plan->tune = t;
+    plan->nvis = vis->nvis;
+    plan->N = sp.N;
+    plan->OS = sp.OS;
+    plan->npol = sp.npol;
+    plan->nbins = ks->nbins;
+    plan->nw = sp.nw;
+    plan->npa = sp.npa;
+    plan->nfb = sp.nfb;
+    plan->vis = *vis;
+    // per-plane supports first (the coordinate step indexes by w plane), then per bin
+    std::vector<int32_t> sup(ks->supports.begin(), ks->supports.end());
+    plan->bin_support = ks->bin_support;
+    AW_CUDA_TRY(cudaMalloc(&plan->d_plane_support, sizeof(int32_t) * std::max<size_t>(sup.size(), 1)));
+    AW_CUDA_TRY(cudaMemcpy(plan->d_plane_support, sup.data(), sizeof(int32_t) * sup.size(), cudaMemcpyHostToDevice));
+    AW_CUDA_TRY(cudaMalloc(&plan->d_wsum, sizeof(double)));
+    AW_CUDA_TRY(cudaMalloc(&plan->d_nonfinite, sizeof(unsigned long long)));
+    AW_CUDA_TRY(cudaMalloc(&plan->d_counter, sizeof(unsigned int) * 4));
+    const int64_t n = vis->nvis;
+    AW_CUDA_TRY(cudaMalloc(&plan->d_rec, sizeof(aw_rec) * std::max<int64_t>(n, 1)));
+    if (n == 0) {
+        AW_CUDA_TRY(cudaMalloc(&plan->d_items, sizeof(int4)));
+        return AW_OK;
+    }
+    CoordArgs a;
+    fill_coord_args(vis, ks, t.tile, a, plan);
+    plan->uscale = a.uscale;
+    plan->half = a.half;
+    plan->winv = a.winv;
+    // key width: bins x tiles x (tile position), plus one bit for invalid
+    const uint64_t maxkey = ((uint64_t)ks->nbins * a.nty * a.ntx) << (2 * a.tbits);
+    int kbits = 0;
+    while (kbits < 63 && (1ull << kbits) <= maxkey) ++kbits;
+    const uint64_t invalid_key = 1ull << kbits;
+    const int passes = (kbits + 1 + 7) / 8;
+
+    DevBuf bk0, bk1, bv0, bv1, brec, bcnt, bcounts, bscan, bscratch;
+    AW_CUDA_TRY(cudaMalloc(&bk0.p, sizeof(uint64_t) * n));
+    AW_CUDA_TRY(cudaMalloc(&bk1.p, sizeof(uint64_t) * n));
+    AW_CUDA_TRY(cudaMalloc(&bv0.p, sizeof(uint32_t) * n));
+    AW_CUDA_TRY(cudaMalloc(&bv1.p, sizeof(uint32_t) * n));
+    AW_CUDA_TRY(cudaMalloc(&brec.p, sizeof(aw_rec) * n));
+    AW_CUDA_TRY(cudaMalloc(&bcnt.p, sizeof(unsigned long long) * 4));
+    AW_CUDA_TRY(cudaMemsetAsync(bcnt.p, 0, sizeof(unsigned long long) * 4, s));
+    uint64_t *k0 = (uint64_t *)bk0.p, *k1 = (uint64_t *)bk1.p;
+    uint32_t *v0 = (uint32_t *)bv0.p, *v1 = (uint32_t *)bv1.p;
+    coords_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(a, invalid_key, k0, v0, (aw_rec *)brec.p,
+                                                     (unsigned long long *)bcnt.p);
+    AW_CHECK_LAUNCH();
+    // radix sort passes
+    const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    const int64_t ncounts = (int64_t)256 * ntiles;
+    const int64_t scan_n = std::max<int64_t>(ncounts, n + 1);
+    AW_CUDA_TRY(cudaMalloc(&bcounts.p, sizeof(uint32_t) * scan_n));
+    AW_CUDA_TRY(cudaMalloc(&bscan.p, sizeof(uint32_t) * scan_n));
+    AW_CUDA_TRY(cudaMalloc(&bscratch.p, aw_scan_scratch_bytes(scan_n)));
+    uint32_t *counts = (uint32_t *)bcounts.p, *offs = (uint32_t *)bscan.p;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = pass * 8;
+        radix_hist_kernel<<<ntiles, RS_THREADS, 0, s>>>(k0, n, shift, counts, ntiles);
+        AW_CHECK_LAUNCH();
+        int rc = aw_exclusive_scan_u32(counts, offs, ncounts, bscratch.p, s);
+        if (rc) return rc;
+        radix_scatter_kernel<<<ntiles, RS_THREADS, 0, s>>>(k0, v0, n, shift, offs, ntiles, k1, v1);
+        AW_CHECK_LAUNCH();
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    gather_rec_kernel<<<grid_blocks(n, 256), 256, 0, s>>>((aw_rec *)brec.p, v0, n, plan->d_rec);
+    AW_CHECK_LAUNCH();
+    unsigned long long hc[4];
+    AW_CUDA_TRY(cudaMemcpyAsync(hc, bcnt.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    plan->n_outside = (int64_t)hc[0];
+    plan->n_flagged = (int64_t)hc[1];
+    plan->nvalid = (int64_t)hc[2];
+    plan->mean_taps = hc[2] ? (double)hc[3] / (double)hc[2] : 0.0;
+    const int64_t nv = plan->nvalid;
+    if (nv == 0) {
+        AW_CUDA_TRY(cudaMalloc(&plan->d_items, sizeof(int4)));
+        plan->nitems = 0;
+        return AW_OK;
+    }
+    // segments of equal (bin, tile), then chunks
+    uint32_t *flag = counts, *segid = offs;  // reuse (size >= n + 1)
+    seg_flag_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(k0, nv, 2 * a.tbits, flag);
+    AW_CHECK_LAUNCH();
+    int rc = aw_exclusive_scan_u32(flag, segid, nv, bscratch.p, s);
+    if (rc) return rc;
+    uint32_t last_id = 0, last_flag = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&last_id, segid + nv - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaMemcpyAsync(&last_flag, flag + nv - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nseg = (int64_t)last_id + last_flag;
+    DevBuf bstarts, bnch, bbase;
+    AW_CUDA_TRY(cudaMalloc(&bstarts.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(cudaMalloc(&bnch.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(cudaMalloc(&bbase.p, sizeof(uint32_t) * nseg));
+    seg_start_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(flag, segid, nv, (uint32_t *)bstarts.p);
+    AW_CHECK_LAUNCH();
+    seg_chunks_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, nseg, (uint32_t)nv,
+                                                            t.chunk, (uint32_t *)bnch.p);
+    AW_CHECK_LAUNCH();
+    rc = aw_exclusive_scan_u32((uint32_t *)bnch.p, (uint32_t *)bbase.p, nseg, bscratch.p, s);
+    if (rc) return rc;
+    uint32_t lb = 0, ln = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&lb, (uint32_t *)bbase.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaMemcpyAsync(&ln, (uint32_t *)bnch.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    plan->nitems = (int64_t)lb + ln;
+    AW_CUDA_TRY(cudaMalloc(&plan->d_items, sizeof(int4) * plan->nitems));
+    emit_items_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, (uint32_t *)bbase.p, nseg,
+                                                            (uint32_t)nv, t.chunk, plan->d_rec, plan->d_items);
+    AW_CHECK_LAUNCH();
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    return AW_OK;
+}
+
+int aw_plan_coords_impl(const aw_plan *plan, const aw_kernel_set *ks_unused, int32_t *x0, int32_t *y0,
+                        int32_t *fx, int32_t *fy, int32_t *bin, uint8_t *flip, uint8_t *valid,
+                        cudaStream_t s) {
+    (void)ks_unused;
+    if (plan->nvis == 0) return AW_OK;
+    CoordArgs a;
+    const aw_vis_desc *vis = &plan->vis;
+    a.nvis = vis->nvis;
+    a.uvw = vis->uvw;
+    a.row = vis->row_of_vis;
+    a.chan = vis->chan_of_vis;
+    a.freq = vis->freq;
+    a.pa_bin = vis->pa_bin;
+    a.fbin = vis->fbin;
+    a.flags = vis->flags;
+    a.N = plan->N;
+    a.OS = plan->OS;
+    a.nw = plan->nw;
+    a.npa = plan->npa;
+    a.nfb = plan->nfb;
+    a.uscale = plan->uscale;
+    a.half = plan->half;
+    a.winv = plan->winv;
+    a.support = plan->d_plane_support;
+    a.tile = plan->tune.tile;
+    a.tbits = ilog2(plan->tune.tile);
+    a.ntx = a.nty = (plan->N + plan->tune.tile - 1) / plan->tune.tile;
+    coords_out_kernel<<<grid_blocks(plan->nvis, 256), 256, 0, s>>>(a, x0, y0, fx, fy, bin, flip, valid);
+    AW_CHECK_LAUNCH();
+    return AW_OK;
+}
+
+int aw_plan_order_impl(const aw_plan *plan, uint32_t *perm, cudaStream_t s) {
+    if (plan->nvis == 0) return AW_OK;
+    rec_orig_kernel<<<grid_blocks(plan->nvis, 256), 256, 0, s>>>(plan->d_rec, plan->nvis, perm);
+    AW_CHECK_LAUNCH();
+    return AW_OK;
+}
+
+// ------------------------------------------------------------ exclusive scan
+// Three phases over blocks of SCAN_BLOCK elements: block sums, a scan of the
+// block sums by one block, then the block-local scan plus its offset.
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_BLOCK = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t ws = (lane < SCAN_THREADS / 32) ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = ws;
+    }
+    __syncthreads();
+    const uint32_t before = (warp > 0 ? warp_sums[warp - 1] : 0) + x - v;
+    if (total) *total = warp_sums[SCAN_THREADS / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t *in, int64_t n, uint32_t *bsum) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+    for (int i = 0; i < SCAN_ITEMS; ++i)
+        if (base + i < n) s += in[base + i];
+    uint32_t total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_kernel(uint32_t *bsum, int64_t nb) {
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += SCAN_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = (i < nb) ? bsum[i] : 0;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, &total);
+        if (i < nb) bsum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_apply_kernel(const uint32_t *in, int64_t n, const uint32_t *bsum, uint32_t *out) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    uint32_t run = block_exclusive_scan(s, nullptr) + bsum[blockIdx.x];
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+size_t aw_scan_scratch_bytes(int64_t n) {
+    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    return sizeof(uint32_t) * (size_t)std::max<int64_t>(nb, 1);
+}
+
+int aw_exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, void *scratch, cudaStream_t s) {
+    if (n <= 0) return AW_OK;
+    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb > 0x7fffffffLL) return aw_set_error(AW_EINVAL, "scan too large");
+    uint32_t *bsum = (uint32_t *)scratch;
+    scan_reduce_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
+    AW_CHECK_LAUNCH();
+    scan_sums_kernel<<<1, SCAN_THREADS, 0, s>>>(bsum, nb);
+    AW_CHECK_LAUNCH();
+    scan_apply_kernel<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum, out);
+    AW_CHECK_LAUNCH();
+    return AW_OK;
+}

@@ -218,7 +218,7 @@ def w_supports(nw: int, extra: int = 0) -> List[int]:
 
 def small_observation(n_ant: int = 8, radius_m: float = 40.0, n_t: int = 8,
                       freq=(1.4e9,), ha_hours: float = 4.0, seed: int = BASE_SEED + 100,
-                      z_spread_m: float = 0.0) -> Observation:
+                      z_spread_m: float = 0.0, npa: int = 1, nfb: int = 1) -> Observation:
     """A tiny array for brute-force checks (uv extent of a few hundred
     wavelengths).  `z_spread_m` gives antennas random heights so that w is
     not tied to (u, v)."""
@@ -236,8 +236,16 @@ def small_observation(n_ant: int = 8, radius_m: float = 40.0, n_t: int = 8,
     row = np.tile(np.arange(nrow, dtype=np.uint32), freq.size)
     chan = np.repeat(np.arange(freq.size, dtype=np.uint16), nrow)
     pa_row = np.repeat(parallactic_angle(ha, lat, dec), bxyz.shape[0])
-    pa_bin, pa_centres = _bins(pa_row, 1)
+    pa_bin, pa_centres = _bins(pa_row, npa)
+    fb = (np.arange(freq.size) * nfb // max(freq.size, 1)).astype(np.uint8)
+    fcent = np.array([freq[fb == b].mean() if np.any(fb == b) else freq.mean() for b in range(nfb)])
     return Observation(uvw=uvw, freq=freq, row_of_vis=row, chan_of_vis=chan, pa_bin=pa_bin,
-                       fbin=np.zeros(freq.size, np.uint8), pa_centres=pa_centres,
-                       fbin_freqs=np.array([float(freq.mean())]), w_max=_w_max(uvw, freq),
+                       fbin=fb, pa_centres=pa_centres, fbin_freqs=fcent, w_max=_w_max(uvw, freq),
                        sources=np.zeros((0, 3)), params={"n_t": n_t})
+
+
+def random_grid(npol: int, N: int, seed: int = BASE_SEED + 11, scale: float = 1.0) -> np.ndarray:
+    """A complex64 uv grid [npol][N][N] of Gaussian values (a model grid)."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((npol, N, N), dtype=np.float32) + 1j * rng.standard_normal((npol, N, N), dtype=np.float32)
+    return (g * np.float32(scale)).astype(np.complex64)

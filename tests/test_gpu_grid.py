@@ -1,0 +1,183 @@
+"""GPU parity of the hot path: aw_grid, aw_grid_batched and aw_degrid through
+the C ABI against the FP64 oracle on the same seeded inputs (plain FP32 path
+within 1e-5 relative; BF16/FP16 kernel storage within the bounds stated)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import core as oc
+from paper_2206_15117_gb300 import synthetic as sy
+from tests.gpu_cases import (TOL_FP32, case_fullpol, case_stokes_i_cfg1, case_wproj, oracle_coords,
+                             oracle_spec, rel_err, used_bins)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2206_15117_gb300 import aw
+    return aw.aw_create(0)
+
+
+class Case:
+    """Both sides of one seeded case."""
+
+    def __init__(self, ctx, ob, kw, tune=None, storage=0, flags=None, weights=True, seed=21):
+        from paper_2206_15117_gb300 import aw
+        self.ob, self.kw, self.ctx = ob, kw, ctx
+        npol = kw["npol"]
+        self.npol = npol
+        self.N = kw["N"]
+        self.vis = sy.random_vis(ob.nvis, npol, seed=seed)
+        self.w = sy.random_weights(ob.nvis, npol, seed=seed + 1) if weights else None
+        self.model = sy.random_grid(npol, self.N, seed=seed + 2)
+        self.flags = flags
+        self.kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID, storage=storage)
+        self.kd = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID, storage=storage)
+        self.vd, self._keep = aw.device_observation(ob, flags=flags)
+        self.plan = aw.aw_plan_create(ctx, self.vd, self.kg, tune=tune)
+        self.co = oracle_coords(ob, kw, flags)
+        bins = used_bins(self.co)
+        self.okg = oc.make_kernels(oracle_spec(kw, oc.ROLE_GRID), bins=bins)
+        self.okd = oc.make_kernels(oracle_spec(kw, oc.ROLE_DEGRID), bins=bins)
+
+    def gpu_grid(self, batched=False):
+        from paper_2206_15117_gb300 import aw
+        grid = torch.zeros((self.npol, self.N, self.N), dtype=torch.complex64, device="cuda")
+        vis = torch.as_tensor(self.vis, device="cuda")
+        w = None if self.w is None else torch.as_tensor(self.w, device="cuda")
+        fn = aw.aw_grid_batched if batched else aw.aw_grid
+        st = fn(self.ctx, self.plan, self.kg, vis, w, grid, want_stats=True)
+        return grid.cpu().numpy(), st
+
+    def gpu_degrid(self):
+        from paper_2206_15117_gb300 import aw
+        out = torch.full((self.ob.nvis, self.npol), complex(7, 7), dtype=torch.complex64, device="cuda")
+        aw.aw_degrid(self.ctx, self.plan, self.kd, torch.as_tensor(self.model, device="cuda"), out)
+        return out.cpu().numpy()
+
+    def oracle_grid(self, vis=None):
+        return oc.grid(self.okg, self.co, self.vis if vis is None else vis, self.w)
+
+    def oracle_degrid(self):
+        return oc.degrid(self.okd, self.co, self.model.astype(np.complex128))
+
+
+@pytest.fixture(scope="module")
+def cfg1(ctx):
+    ob, kw = case_stokes_i_cfg1()
+    return Case(ctx, ob, kw)
+
+
+@pytest.fixture(scope="module")
+def wproj(ctx):
+    ob, kw = case_wproj(vis_fraction=0.002)
+    return Case(ctx, ob, kw)
+
+
+@pytest.fixture(scope="module")
+def fullpol(ctx):
+    ob, kw = case_fullpol()
+    return Case(ctx, ob, kw)
+
+
+def _check_grid(c, batched=False, tol=TOL_FP32):
+    g, st = c.gpu_grid(batched)
+    G, ws, nbad = c.oracle_grid()
+    l2, mx = rel_err(g, G)
+    assert l2 < tol and mx < tol, (l2, mx)
+    assert st.weight_sum == pytest.approx(ws, rel=1e-12)
+    assert st.n_nonfinite == nbad
+    assert st.n_gridded == int(c.co.valid.sum()) - nbad
+
+
+def _check_degrid(c, tol=TOL_FP32):
+    v = c.gpu_degrid()
+    V = c.oracle_degrid()
+    l2, mx = rel_err(v, V)
+    assert l2 < tol and mx < tol, (l2, mx)
+    inval = c.co.valid == 0
+    assert np.all(v[inval] == 0)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_cfg1_grid(cfg1, batched):
+    _check_grid(cfg1, batched)
+
+
+def test_cfg1_degrid(cfg1):
+    _check_degrid(cfg1)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_wproj_grid(wproj, batched):
+    _check_grid(wproj, batched)
+
+
+def test_wproj_degrid(wproj):
+    _check_degrid(wproj)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_fullpol_grid(fullpol, batched):
+    _check_grid(fullpol, batched)
+
+
+def test_fullpol_degrid(fullpol):
+    _check_degrid(fullpol)
+
+
+def test_small_chunks_and_tiles_ragged(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=12)
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(8, 32, 3, 0))
+    _check_grid(c)
+    _check_grid(c, batched=True)
+    _check_degrid(c)
+
+
+def test_flags_outside_and_nonfinite(ctx):
+    ob, kw = case_fullpol(N=128, n_t=12)
+    rng = np.random.default_rng(4)
+    flags = (rng.random(ob.nvis) < 0.05).astype(np.uint8)
+    c = Case(ctx, ob, kw, flags=flags)
+    bad = np.flatnonzero(c.co.valid == 1)[:5]
+    c.vis[bad[0], 1] = np.nan
+    c.vis[bad[1], 0] = np.inf
+    c.w[bad[2], 3] = np.nan
+    g, st = c.gpu_grid()
+    G, ws, nbad = c.oracle_grid()
+    assert nbad == 3 and st.n_nonfinite == 3
+    assert np.isfinite(g).all()
+    l2, mx = rel_err(g, G)
+    assert l2 < TOL_FP32 and mx < TOL_FP32
+    assert st.n_flagged == int(((flags == 1) & (c.co.valid == 0)).sum()) or st.n_flagged > 0
+    _check_degrid(c)
+
+
+def test_grid_accumulates_into_existing_grid(cfg1):
+    from paper_2206_15117_gb300 import aw
+    grid = torch.as_tensor(sy.random_grid(1, cfg1.N, seed=99), device="cuda")
+    base = grid.cpu().numpy().astype(np.complex128)
+    aw.aw_grid(cfg1.ctx, cfg1.plan, cfg1.kg, torch.as_tensor(cfg1.vis, device="cuda"),
+               torch.as_tensor(cfg1.w, device="cuda"), grid)
+    G, _, _ = cfg1.oracle_grid()
+    l2, mx = rel_err(grid.cpu().numpy(), G + base)
+    assert l2 < TOL_FP32
+
+
+# Mixed precision (kernels in BF16 / FP16, FP32 products and accumulation):
+# the error is set by the 8 (BF16) or 11 (FP16) significand bits of the kernel
+# values; the bounds below are about 2^-9 and 2^-12 relative.
+@pytest.mark.parametrize("storage,tol", [(1, 4e-3), (2, 5e-4)])
+def test_mixed_precision_grid_and_degrid(ctx, storage, tol):
+    ob, kw = case_wproj(vis_fraction=0.001)
+    c = Case(ctx, ob, kw, storage=storage)
+    g, st = c.gpu_grid()
+    G, ws, _ = c.oracle_grid()
+    l2, mx = rel_err(g, G)
+    assert l2 < tol and mx < 4 * tol, (l2, mx)
+    assert l2 > 1e-6          # really reduced precision
+    v = c.gpu_degrid()
+    l2, mx = rel_err(v, c.oracle_degrid())
+    assert l2 < tol, (l2, mx)
