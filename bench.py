@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of full-polarisation AW-projection gridding + degridding on GB300.
+
+Workload (default): 4 linear correlations, 16 Mueller A-kernels from an Airy
+beam (12 m dish) with 1 % complex leakage, Eq. 6 regularised inverse for
+gridding, 32 w planes x 8 parallactic-angle bins x 4 beam-frequency bins
+(1024 bins, supports 16..72 cells, oversampling 8), 288 channels of uneven
+visibility counts (~64M visibilities), 4096 x 4096 x 4 complex64 grid.
+Synthetic ASKAP-shaped geometry (see paper_2206_15117_gb300.synthetic);
+visibility values are seeded complex Gaussian noise (the work does not depend
+on them).
+
+One step = one Cotton-Schwab major-cycle pass of the hot path: zero the grid,
+aw_grid_batched (persistent, graph-captured, autotuned), aw_fft_to_image,
+aw_degrid.  Kernel synthesis and the visibility sort run once per dataset
+before the timed region and are reported separately.
+
+`--impl reference` times the FP64 CPU oracle instead (see cpu_baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mvis/s grid+degrid (full-pol AW; FP32 vs mixed vs learned) and % of roofline"
+UNIT = "Mvis/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--time-samples", type=int, default=2000, help="scale the workload (2000 = full)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 table variants")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+def workload(time_samples: int):
+    from paper_2206_15117_gb300 import synthetic as sy
+    ob = sy.observation(3, time_samples=time_samples)
+    g = sy.grid_geometry(3)
+    nw = 32
+    kw = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=7.0, npol=4, nw=nw, w_max=ob.w_max,
+              supports=sy.w_supports(nw, extra=8), pa=list(ob.pa_centres),
+              fbin_freqs=list(ob.fbin_freqs), dish_d=12.0, d_xy=0.01 * np.exp(0.4j),
+              d_yx=0.01 * np.exp(-1.3j), eps=0.2)
+    return ob, kw
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "0x1"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(ob, kw, cpu_seconds: float, seed: int = 5):
+    """A bounded sample of the workload for the FP64 oracle: every visibility
+    of a few seeded bins (capped), with the oracle's own kernels for them."""
+    from oracle import core as oc
+    from paper_2206_15117_gb300 import synthetic as sy
+    rng = np.random.default_rng(seed)
+    sub = np.sort(rng.choice(ob.nvis, size=min(ob.nvis, 2_000_000), replace=False))
+    spec = oc.KernelSpec(**kw)
+    co = oc.coords(spec, ob.uvw, ob.row_of_vis[sub], ob.chan_of_vis[sub], ob.freq, ob.pa_bin, ob.fbin)
+    ok = co.valid == 1
+    bins, counts = np.unique(co.bin[ok], return_counts=True)
+    pick = rng.choice(bins, size=min(4, bins.size), replace=False, p=counts / counts.sum())
+    sup = np.array(spec.supports)
+    S2_all = float(np.mean(sup[co.bin[ok] // (spec.npa * spec.nfb)].astype(np.float64) ** 2))
+    # per-visibility cost of grid + degrid is about 2 * 16 * S^2 complex MACs
+    budget_macs = cpu_seconds * 2.0e8
+    sel = []
+    for b in pick:
+        idx = np.flatnonzero(ok & (co.bin == b))
+        S = sup[b // (spec.npa * spec.nfb)]
+        cap = max(16, int(budget_macs / len(pick) / (32.0 * S * S)))
+        sel.append(idx[:cap])
+    sel = np.concatenate(sel)
+    keep = sub[sel]
+    rows, chans = ob.row_of_vis[keep], ob.chan_of_vis[keep]
+    cos = oc.coords(spec, ob.uvw, rows, chans, ob.freq, ob.pa_bin, ob.fbin)
+    kg = oc.make_kernels(oc.KernelSpec(**kw, role=oc.ROLE_GRID), bins=pick)
+    kd = oc.make_kernels(oc.KernelSpec(**kw, role=oc.ROLE_DEGRID), bins=pick)
+    vis = sy.random_vis(keep.size, 4, seed=seed + 1)
+    model = sy.random_grid(4, kw["N"], seed=seed + 2).astype(np.complex128)
+    S2_sample = float(np.mean(sup[cos.bin[cos.valid == 1] // (spec.npa * spec.nfb)].astype(np.float64) ** 2))
+    return dict(co=cos, kg=kg, kd=kd, vis=vis, model=model, n=int(keep.size), bins=[int(b) for b in pick],
+                S2_sample=S2_sample, S2_all=S2_all)
+
+
+def oracle_step(smp):
+    from oracle import core as oc
+    t0 = time.perf_counter()
+    oc.grid(smp["kg"], smp["co"], smp["vis"])
+    oc.degrid(smp["kd"], smp["co"], smp["model"])
+    return time.perf_counter() - t0
+
+
+def oracle_mvis(smp, seconds):
+    # scaled from the sample's mean S^2 to the workload's (the oracle's cost is
+    # proportional to the taps per visibility)
+    return smp["n"] / seconds / 1e6 * smp["S2_sample"] / smp["S2_all"]
+
+
+def sample_text(smp):
+    return ("%d visibilities of bins %s of the same workload (mean S^2 %.0f vs %.0f for all); "
+            "Mvis/s scaled by that S^2 ratio; FP64 C loops, one thread" %
+            (smp["n"], smp["bins"], smp["S2_sample"], smp["S2_all"]))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import build as ob_build
+    ob_build.build()
+    ob, kw = workload(args.time_samples)
+    per_step = max(1.0, min(args.cpu_seconds, 180.0 / max(1, args.steps + args.warmup)))
+    smp = oracle_sample(ob, kw, per_step)
+    for _ in range(args.warmup):
+        oracle_step(smp)
+    ts = [oracle_step(smp) for _ in range(args.steps)]
+    t = statistics.median(ts)
+    val = oracle_mvis(smp, t)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(ob, kw, None),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample_text(smp)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(ob, kw, info):
+    cfg = {"workload": "full-pol AW grid+FFT+degrid, 4096^2 x 4 grid, 1024 bins (32 w x 8 PA x 4 freq), "
+                       "supports 16-72, OS 8, 288 channels of uneven counts",
+           "nvis": int(ob.nvis), "N": kw["N"], "npol": 4, "nbins": 32 * len(kw["pa"]) * len(kw["fbin_freqs"]),
+           "OS": kw["OS"], "supports": list(kw["supports"]),
+           "l2": "inputs larger than L2 (visibilities 2 GB, kernel tables 33 GB)"}
+    if info is not None:
+        cfg.update({"nvalid": int(info.nvalid), "mean_taps": round(info.mean_taps, 1),
+                    "tile": info.tile, "chunk": info.chunk})
+    return cfg
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import build as awbuild
+
+    awbuild.build()
+    dev_index = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev_index)
+    dev = torch.device("cuda", dev_index)
+    stream = torch.cuda.current_stream()
+    ctx = aw.aw_create(dev_index)
+    ob, kw = workload(args.time_samples)
+    if world > 1:   # weak scaling: every rank its own seeded replica
+        from paper_2206_15117_gb300 import synthetic as sy
+        ob = sy.observation(3, time_samples=args.time_samples, seed=sy.BASE_SEED + 3 + 1000 * rank)
+    nvis = ob.nvis
+    t0 = time.perf_counter()
+    kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
+    kd = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID)
+    t_synth = time.perf_counter() - t0
+    kinfo = aw.aw_kernel_set_info(kg)
+    vd, keep = aw.device_observation(ob, dev)
+    # autotune on every visibility of 2 of the 32 (PA, frequency) bin pairs:
+    # about a tenth of the data with the same density per (bin, tile) and the
+    # same support mix; then the full plan
+    from paper_2206_15117_gb300 import synthetic as sy
+    sub = np.flatnonzero((ob.pa_bin[ob.row_of_vis] == 0) & (ob.fbin[ob.chan_of_vis] < 2))
+    ob_sub = sy.Observation(**{**ob.__dict__, "row_of_vis": ob.row_of_vis[sub], "chan_of_vis": ob.chan_of_vis[sub]})
+    vd_sub, keep_sub = aw.device_observation(ob_sub, dev)
+    t0 = time.perf_counter()
+    tune = aw.aw_autotune(ctx, vd_sub, kg)
+    t_tune = time.perf_counter() - t0
+    del vd_sub, keep_sub
+    t0 = time.perf_counter()
+    plan = aw.aw_plan_create(ctx, vd, kg, tune=tune)
+    t_plan = time.perf_counter() - t0
+    info = aw.aw_plan_query(plan)
+    N = kw["N"]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2206_15117 + rank)
+    vis = torch.randn((nvis, 4), dtype=torch.complex64, device=dev, generator=gen)
+    vis_out = torch.empty_like(vis)
+    model = torch.randn((4, N, N), dtype=torch.complex64, device=dev, generator=gen)
+    grid = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
+    image = torch.empty((4, N, N), dtype=torch.float32, device=dev)
+    launches_per_step = 4   # grid (persistent), checker + grid-correction (FFT step), degrid
+
+    def step(ev=None, kset_g=kg, kset_d=kd):
+        grid.zero_()
+        if ev: ev[0].record(stream)
+        st = aw.aw_grid_batched(ctx, plan, kset_g, vis, None, grid)
+        if ev: ev[1].record(stream)
+        aw.aw_fft_to_image(ctx, kset_g, grid, float(info.nvalid), image)
+        if ev: ev[2].record(stream)
+        aw.aw_degrid(ctx, plan, kset_d, model, vis_out)
+        if ev: ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(dev_index)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    total_ms = e_start.elapsed_time(e_end)
+    t_grid = [e[0].elapsed_time(e[1]) for e in evs]
+    t_fft = [e[1].elapsed_time(e[2]) for e in evs]
+    t_deg = [e[2].elapsed_time(e[3]) for e in evs]
+    if dist:
+        import torch.distributed as tdist
+        tt = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nvis / (ms_per_step / 1e3) / 1e6
+
+    # roofline of the dominant kernel: FP32 ALU (complex MACs of the Mueller product)
+    flops = 128.0 * info.mean_taps * info.nvalid          # 16 complex MACs x 8 flop per tap
+    g_ms, d_ms = statistics.mean(t_grid), statistics.mean(t_deg)
+    dom_ms = max(g_ms, d_ms)
+    dom = "aw_grid (persistent gridding kernel)" if g_ms >= d_ms else "aw_degrid (warp-per-visibility)"
+    peak_tflops = fp32_peak_tflops()
+    achieved = flops / (dom_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None,
+            "peak_source": "FP32 CUDA-core peak derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "flops_per_launch": flops}
+
+    # variants: BF16 / FP16 kernel tables (FP32 arithmetic)
+    variants = {"fp32": {"grid_ms": g_ms, "degrid_ms": d_ms, "mvis_s": nvis / ((g_ms + d_ms) / 1e3) / 1e6}}
+    if not args.no_variants:
+        for name, stg in (("bf16", aw.AW_STORAGE_BF16), ("fp16", aw.AW_STORAGE_FP16)):
+            kg2 = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID, storage=stg)
+            kd2 = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID, storage=stg)
+            step(None, kg2, kd2)
+            ev2 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(3)]
+            for k in range(3):
+                step(ev2[k], kg2, kd2)
+            torch.cuda.synchronize()
+            gm = statistics.mean(e[0].elapsed_time(e[1]) for e in ev2)
+            dm = statistics.mean(e[2].elapsed_time(e[3]) for e in ev2)
+            variants[name] = {"grid_ms": gm, "degrid_ms": dm, "mvis_s": nvis / ((gm + dm) / 1e3) / 1e6,
+                              "table_bytes": int(aw.aw_kernel_set_info(kg2).bytes)}
+            del kg2, kd2
+            torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        vis_host = torch.empty((nvis, 4), dtype=torch.complex64, pin_memory=True)
+        vis_host.copy_(vis)
+        out_host = torch.empty((nvis, 4), dtype=torch.complex64, pin_memory=True)
+        vis_dev = torch.empty_like(vis)
+        ne = min(args.steps, 3)
+
+        def e2e_step():
+            vis_dev.copy_(vis_host, non_blocking=True)
+            grid.zero_()
+            aw.aw_grid_batched(ctx, plan, kg, vis_dev, None, grid)
+            aw.aw_fft_to_image(ctx, kg, grid, float(info.nvalid), image)
+            aw.aw_degrid(ctx, plan, kd, model, vis_out)
+            out_host.copy_(vis_out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ne):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / ne
+        nbytes = vis_host.numel() * 8
+        e2e = {"value": world * nvis / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
+               "d2h_bytes_per_step": int(nbytes), "ms_per_step": e_ms,
+               "how": "pinned host visibilities copied in, grid + FFT + degrid, predicted visibilities copied out"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        smp = oracle_sample(ob, kw, args.cpu_seconds)
+        ts = [oracle_step(smp)]
+        cpu = {"value": oracle_mvis(smp, ts[0]), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample_text(smp), "seconds": ts[0]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(ob, kw, info),
+                "parallelism": "replicas" if world > 1 else "single",
+                "breakdown_ms": {"grid": g_ms, "fft_to_image": statistics.mean(t_fft), "degrid": d_ms},
+                "once_per_dataset_s": {"kernel_synthesis_grid_and_degrid": t_synth, "autotune": t_tune,
+                                       "plan_sort": t_plan, "table_bytes_per_set": int(kinfo.bytes)},
+                "roofline": roof, "variants": variants, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                           "reasons": clocks["reasons"]},
+                "gpu_launches": launches_per_step * args.steps,
+                "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm}}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def fp32_peak_tflops():
+    try:
+        j = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mhz = float(j.get("sm_max_mhz", 2070.0))
+    except Exception:
+        mhz = 2070.0
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            tdist.init_process_group("nccl")
+        else:
+            tdist.init_process_group("gloo")
+        dist = tdist
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world, dist)
+    if dist:
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())
