@@ -308,6 +308,29 @@ int aw_fft_to_image(aw_ctx *ctx, const aw_kernel_set *kset, void *grid, double w
 int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, float eps,
                  float *gamma, void *stream);
 
+/*
+ * mosaic_gamma_noalloc - mosaic_gamma for callers that cannot allocate device
+ * memory: code running while a stream is captured into a CUDA graph, code
+ * inside a framework whose allocator owns the device memory, real-time loops
+ * that forbid allocation after start-up.  It needs no aw_ctx (aw_create
+ * allocates) and calls no cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart; this is a deployment variant of the Eq. 1 call
+ * above, with the same arguments and result.
+ *
+ * Scratch: a fixed file-scope device array of 4097 floats (16 KB) inside
+ * libaw, held by every GPU that loads the library until the process exits.
+ * Limit: N * N <= 4096 * 4096 pixels; larger images return AW_EINVAL before
+ * any GPU work.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the one array and
+ * nothing in it needs to start at zero (each pass reads only slots written
+ * earlier in the same call), but calls whose GPU work overlaps (different
+ * streams or host threads) race on it: serialise them.  beams: device float
+ * [nfield][N][N]; gamma: device float [N][N]; work is enqueued on `stream`.
+ */
+int mosaic_gamma_noalloc(const float *beams, int32_t nfield, int32_t N, float eps, float *gamma,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,7 @@ SIGNATURES = {
     "aw_autotune": (ctypes.c_int, [c_p, ctypes.POINTER(aw_vis_desc), c_p, ctypes.POINTER(aw_tune), c_p]),
     "aw_fft_to_image": (ctypes.c_int, [c_p, c_p, c_p, c_dbl, c_p, c_p]),
     "mosaic_gamma": (ctypes.c_int, [c_p, c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
+    "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
 }
 
 _lib = None
@@ -299,6 +300,14 @@ def mosaic_gamma(ctx: Handle, beams, eps: float, gamma, stream=None):
     nfield, N = int(beams.shape[0]), int(beams.shape[-1])
     _check(load().mosaic_gamma(ctx.ptr, _ptr(beams), nfield, N, ctypes.c_float(eps), _ptr(gamma),
                                _stream(stream)), "mosaic_gamma")
+
+
+def mosaic_gamma_noalloc(beams, eps: float, gamma, stream=None):
+    """mosaic_gamma without a context and without any device allocation (for
+    callers that cannot allocate); see include/aw.h for the scratch rules."""
+    nfield, N = int(beams.shape[0]), int(beams.shape[-1])
+    _check(load().mosaic_gamma_noalloc(_ptr(beams), nfield, N, ctypes.c_float(eps), _ptr(gamma),
+                                       _stream(stream)), "mosaic_gamma_noalloc")
 
 
 def device_observation(ob, device="cuda:0", flags=None):
