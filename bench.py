@@ -50,13 +50,23 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--subset", action="store_true",
+                    help="profiling case: only the visibilities of one (PA, frequency) bin pair, with its "
+                         "32 w-plane kernels (same per-bin density and tables, 1/32 of the memory)")
+    ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm (skips the autotuner)")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------------------- workload
-def workload(time_samples: int):
+def workload(time_samples: int, subset: bool = False):
     from paper_2206_15117_gb300 import synthetic as sy
     ob = sy.observation(3, time_samples=time_samples)
+    if subset:
+        a, f = 3, 1
+        keep = np.flatnonzero((ob.pa_bin[ob.row_of_vis] == a) & (ob.fbin[ob.chan_of_vis] == f))
+        ob = sy.Observation(**{**ob.__dict__, "row_of_vis": ob.row_of_vis[keep], "chan_of_vis": ob.chan_of_vis[keep],
+                               "pa_bin": np.zeros_like(ob.pa_bin), "fbin": np.zeros_like(ob.fbin),
+                               "pa_centres": ob.pa_centres[a:a + 1], "fbin_freqs": ob.fbin_freqs[f:f + 1]})
     g = sy.grid_geometry(3)
     nw = 32
     kw = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=7.0, npol=4, nw=nw, w_max=ob.w_max,
@@ -131,17 +141,21 @@ def oracle_sample(ob, kw, cpu_seconds: float, seed: int = 5):
     bins, counts = np.unique(co.bin[ok], return_counts=True)
     pick = rng.choice(bins, size=min(4, bins.size), replace=False, p=counts / counts.sum())
     sup = np.array(spec.supports)
-    S2_all = float(np.mean(sup[co.bin[ok] // (spec.npa * spec.nfb)].astype(np.float64) ** 2))
-    # per-visibility cost of grid + degrid is about 2 * 16 * S^2 complex MACs
-    budget_macs = cpu_seconds * 2.0e8
+    per = spec.npa * spec.nfb
+    S2_all = float(np.mean(sup[co.bin[ok] // per].astype(np.float64) ** 2))
+    # every visibility of the picked bins: the rows/channels of their (PA, frequency)
+    # bin pairs, then the oracle's own coordinates
     sel = []
+    budget_macs = cpu_seconds * 2.0e9     # grid + degrid cost ~ 2 x 16 S^2 complex MACs per visibility
     for b in pick:
-        idx = np.flatnonzero(ok & (co.bin == b))
-        S = sup[b // (spec.npa * spec.nfb)]
+        a_, f_ = (b // spec.nfb) % spec.npa, b % spec.nfb
+        cand = np.flatnonzero((ob.pa_bin[ob.row_of_vis] == a_) & (ob.fbin[ob.chan_of_vis] == f_))
+        c2 = oc.coords(spec, ob.uvw, ob.row_of_vis[cand], ob.chan_of_vis[cand], ob.freq, ob.pa_bin, ob.fbin)
+        idx = cand[(c2.valid == 1) & (c2.bin == b)]
+        S = sup[b // per]
         cap = max(16, int(budget_macs / len(pick) / (32.0 * S * S)))
         sel.append(idx[:cap])
-    sel = np.concatenate(sel)
-    keep = sub[sel]
+    keep = np.sort(np.concatenate(sel))
     rows, chans = ob.row_of_vis[keep], ob.chan_of_vis[keep]
     cos = oc.coords(spec, ob.uvw, rows, chans, ob.freq, ob.pa_bin, ob.fbin)
     kg = oc.make_kernels(oc.KernelSpec(**kw, role=oc.ROLE_GRID), bins=pick)
@@ -178,7 +192,7 @@ def run_reference(args, rank, world):
         return 0
     from oracle import build as ob_build
     ob_build.build()
-    ob, kw = workload(args.time_samples)
+    ob, kw = workload(args.time_samples, args.subset)
     per_step = max(1.0, min(args.cpu_seconds, 180.0 / max(1, args.steps + args.warmup)))
     smp = oracle_sample(ob, kw, per_step)
     for _ in range(args.warmup):
@@ -221,7 +235,7 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", dev_index)
     stream = torch.cuda.current_stream()
     ctx = aw.aw_create(dev_index)
-    ob, kw = workload(args.time_samples)
+    ob, kw = workload(args.time_samples, args.subset)
     if world > 1:   # weak scaling: every rank its own seeded replica
         from paper_2206_15117_gb300 import synthetic as sy
         ob = sy.observation(3, time_samples=args.time_samples, seed=sy.BASE_SEED + 3 + 1000 * rank)
@@ -240,7 +254,10 @@ def run_ours(args, rank, world, dist):
     ob_sub = sy.Observation(**{**ob.__dict__, "row_of_vis": ob.row_of_vis[sub], "chan_of_vis": ob.chan_of_vis[sub]})
     vd_sub, keep_sub = aw.device_observation(ob_sub, dev)
     t0 = time.perf_counter()
-    tune = aw.aw_autotune(ctx, vd_sub, kg)
+    if args.tune:
+        tune = aw.aw_tune(*[int(x) for x in args.tune.split(",")], 0)
+    else:
+        tune = aw.aw_autotune(ctx, vd_sub, kg)
     t_tune = time.perf_counter() - t0
     del vd_sub, keep_sub
     t0 = time.perf_counter()
@@ -278,11 +295,13 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
+    torch.cuda.nvtx.range_push("timed")
     e_start.record(stream)
     for k in range(args.steps):
         step(evs[k])
     e_end.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
     if dist:
         dist.barrier()

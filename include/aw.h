@@ -165,8 +165,10 @@ int aw_destroy(aw_ctx *ctx);
  * points over the field (M the smallest power of two >= 2 S_p, >= 16; the
  * l = -F/2 row and column set to 0), zero-padded to (M OS)^2, transformed
  * with a double-precision FFT, scaled by 1/M^2 and cut to S_p x S_p taps at
- * OS x OS fine offsets.  Table layout per bin: [OS][OS][S][S][npol*npol],
- * Mueller index out * npol + in.  A visibility at oversampled coordinate Xi
+ * OS x OS fine offsets.  Canonical table order per bin (aw_kernel_set_import
+ * and _export): [OS][OS][S][S][npol*npol], Mueller index out * npol + in;
+ * inside the library the values of one (bin, offset) block are stored in
+ * 16-byte chunks, chunk-major and tap-minor, for coalesced loads.  A visibility at oversampled coordinate Xi
  * covers cells x0..x0+S-1, x0 = floor((Xi - rho)/OS), rho = (S-2) OS/2; tap j
  * holds the kernel at j OS - rho - fx oversampled units (fx the fine offset).
  * Mueller algebra per pixel in FP64: J = E(r) [[1, d_xy], [d_yx, 1]] R(chi),

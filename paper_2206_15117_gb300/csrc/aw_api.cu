@@ -140,9 +140,13 @@ int aw_kernel_set_import(aw_ctx *ctx, const aw_kernel_spec *spec, const void *ta
         rc = aw_table_absmax(reinterpret_cast<const float2 *>(tables), k->total_elems, &mx, S_(stream));
         if (rc == AW_OK && mx > 0.f) k->scale = (float)std::ldexp(1.0, (int)std::floor(-std::log2((double)mx)));
     }
-    if (rc == AW_OK)
-        rc = aw_convert_table_scaled(reinterpret_cast<const float2 *>(tables), k->d_table, k->total_elems,
-                                     k->spec.storage, k->scale, S_(stream));
+    for (int b = 0; rc == AW_OK && b < k->nbins; ++b) {
+        const int S = k->bin_support[b];
+        const char *src = static_cast<const char *>(tables) + k->bin_offset[b] * sizeof(float2);
+        char *dst = static_cast<char *>(k->d_table) + k->bin_offset[b] * k->elem_bytes;
+        rc = aw_convert_table_scaled(reinterpret_cast<const float2 *>(src), dst, (int64_t)k->spec.OS * k->spec.OS,
+                                     S * S, k->P, k->ce, k->spec.storage, k->scale, S_(stream));
+    }
     if (rc == AW_OK) {
         cudaError_t e = cudaStreamSynchronize(S_(stream));
         if (e != cudaSuccess) rc = aw_set_error(AW_ECUDA, "import: %s", cudaGetErrorString(e));
@@ -162,8 +166,9 @@ int aw_kernel_set_export(const aw_kernel_set *k, int32_t bin, void *dst, void *s
     const int S = k->bin_support[bin];
     const int64_t n = (int64_t)k->spec.OS * k->spec.OS * S * S * k->P;
     const char *src = static_cast<const char *>(k->d_table) + k->bin_offset[bin] * k->elem_bytes;
-    return aw_export_table(src, reinterpret_cast<float2 *>(dst), n, k->spec.storage, 1.0f / k->scale,
-                           S_(stream));
+    (void)n;
+    return aw_export_table(src, reinterpret_cast<float2 *>(dst), (int64_t)k->spec.OS * k->spec.OS, S * S, k->P,
+                           k->ce, k->spec.storage, 1.0f / k->scale, S_(stream));
     AW_GUARD_END
 }
 

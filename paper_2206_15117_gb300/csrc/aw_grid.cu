@@ -40,51 +40,50 @@ struct KTraits<AW_STORAGE_FP16> {
     using T = __half2;
 };
 
-// Load P consecutive complex kernel values as float2.
+// Load the P Mueller values of tap `tap` of a (bin, fy, fx) block of L taps
+// that starts at complex element `base_idx`, in the chunked layout of
+// aw_tab_index: chunk c of every tap is contiguous over taps, so lanes that
+// handle consecutive taps issue coalesced 16-byte loads.
 template <int ST, int P>
-__device__ __forceinline__ void load_k(const void *base, int64_t idx, float2 (&k)[P]) {
+__device__ __forceinline__ void load_k(const void *base, int64_t base_idx, int L, int tap, float2 (&k)[P]) {
     if constexpr (ST == AW_STORAGE_FP32) {
-        const float2 *p = reinterpret_cast<const float2 *>(base) + idx;
+        const float2 *p = reinterpret_cast<const float2 *>(base) + base_idx;
         if constexpr (P % 2 == 0) {
 #pragma unroll
-            for (int i = 0; i < P / 2; ++i) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + i);
-                k[2 * i] = make_float2(v.x, v.y);
-                k[2 * i + 1] = make_float2(v.z, v.w);
+            for (int c = 0; c < P / 2; ++c) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(p + 2 * ((int64_t)c * L + tap)));
+                k[2 * c] = make_float2(v.x, v.y);
+                k[2 * c + 1] = make_float2(v.z, v.w);
             }
         } else {
-#pragma unroll
-            for (int i = 0; i < P; ++i) k[i] = __ldg(p + i);
+            k[0] = __ldg(p + tap);
         }
     } else {
-        const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + idx;
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(base) + base_idx;
         if constexpr (P % 4 == 0) {
 #pragma unroll
-            for (int i = 0; i < P / 4; ++i) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + i);
+            for (int c = 0; c < P / 4; ++c) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p + 4 * ((int64_t)c * L + tap)));
                 const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if constexpr (ST == AW_STORAGE_BF16) {
                         __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[j]);
-                        k[4 * i + j] = __bfloat1622float2(h);
+                        k[4 * c + j] = __bfloat1622float2(h);
                     } else {
                         __half2 h = *reinterpret_cast<const __half2 *>(&w[j]);
-                        k[4 * i + j] = __half22float2(h);
+                        k[4 * c + j] = __half22float2(h);
                     }
                 }
             }
         } else {
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-                const uint32_t w = __ldg(p + i);
-                if constexpr (ST == AW_STORAGE_BF16) {
-                    __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w);
-                    k[i] = __bfloat1622float2(h);
-                } else {
-                    __half2 h = *reinterpret_cast<const __half2 *>(&w);
-                    k[i] = __half22float2(h);
-                }
+            const uint32_t w = __ldg(p + tap);
+            if constexpr (ST == AW_STORAGE_BF16) {
+                __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w);
+                k[0] = __bfloat1622float2(h);
+            } else {
+                __half2 h = *reinterpret_cast<const __half2 *>(&w);
+                k[0] = __half22float2(h);
             }
         }
     }
@@ -117,9 +116,10 @@ struct GridArgs {
 
 template <int NPOL>
 struct SmemLayout {
-    // per staged visibility: x0|y0<<16, (x0 mod S)|(y0 mod S)<<16, kernel offset, values
+    // per staged visibility: int4 {x0 | y0 << 16, (x0 mod S) | (y0 mod S) << 16,
+    // kernel block offset, 0} and NPOL weighted complex values
     static __host__ __device__ size_t bytes(int chunk) {
-        return (size_t)chunk * (3 * sizeof(int) + NPOL * sizeof(float2));
+        return (size_t)chunk * (sizeof(int4) + NPOL * sizeof(float2));
     }
 };
 
@@ -130,10 +130,8 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
     const int start = it.x, count = it.y, bin = it.z;
     const int S = a.bin_support[bin];
     const int64_t tab0 = a.bin_offset[bin];
-    int *s_pos = reinterpret_cast<int *>(smem);
-    int *s_mod = s_pos + a.chunk;
-    int *s_koff = s_mod + a.chunk;
-    float2 *s_v = reinterpret_cast<float2 *>(s_koff + a.chunk);
+    int4 *s_meta = reinterpret_cast<int4 *>(smem);
+    float2 *s_v = reinterpret_cast<float2 *>(s_meta + a.chunk);
     // ---- stage the item's visibilities
     double wloc = 0.0;
     unsigned long long nbad = 0;
@@ -169,9 +167,8 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
             s_v[i * NPOL + c] = make_float2(ws * v[c].x, ws * v[c].y);
         }
         wloc += wm / NPOL;
-        s_pos[i] = (int)r.x0 | ((int)r.y0 << 16);
-        s_mod[i] = ((int)r.x0 % S) | (((int)r.y0 % S) << 16);
-        s_koff[i] = ((int)r.fy * a.OS + (int)r.fx) * S * S * P;
+        s_meta[i] = make_int4((int)r.x0 | ((int)r.y0 << 16), ((int)r.x0 % S) | (((int)r.y0 % S) << 16),
+                              ((int)r.fy * a.OS + (int)r.fx) * S * S * P, 0);
     }
     // block reduction of the weight sum (double) and the non-finite count
     for (int o = 16; o; o >>= 1) {
@@ -192,8 +189,6 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
     const int NT = blockDim.x;
     const int G = (L >= NT) ? 1 : min(NT / L, 32);
     const int active = (L >= NT) ? NT : G * L;
-    const float2 *kt = nullptr;
-    (void)kt;
     if ((int)threadIdx.x < active) {
         const int g = (L >= NT) ? 0 : (int)threadIdx.x / L;
         const int q0 = (L >= NT) ? (int)threadIdx.x : (int)threadIdx.x % L;
@@ -205,8 +200,9 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
 #pragma unroll
             for (int s = 0; s < NPOL; ++s) acc[s] = make_float2(0.f, 0.f);
             for (int i = g; i < count; i += G) {
-                const int pos = s_pos[i];
-                const int md = s_mod[i];
+                const int4 meta = s_meta[i];
+                const int pos = meta.x;
+                const int md = meta.y;
                 int jx = ca - (md & 0xffff);
                 jx += (jx < 0) ? S : 0;
                 int jy = cb - (md >> 16);
@@ -226,10 +222,16 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
                     for (int s = 0; s < NPOL; ++s) acc[s] = make_float2(0.f, 0.f);
                 }
                 float2 k[P];
-                load_k<ST, P>(a.ktab, tab0 + s_koff[i] + (int64_t)(jy * S + jx) * P, k);
+                load_k<ST, P>(a.ktab, tab0 + meta.z, L, jy * S + jx, k);
                 float2 v[NPOL];
-#pragma unroll
-                for (int c = 0; c < NPOL; ++c) v[c] = s_v[i * NPOL + c];
+                if constexpr (NPOL == 4) {
+                    const float4 v01 = reinterpret_cast<const float4 *>(s_v)[2 * i];
+                    const float4 v23 = reinterpret_cast<const float4 *>(s_v)[2 * i + 1];
+                    v[0] = make_float2(v01.x, v01.y); v[1] = make_float2(v01.z, v01.w);
+                    v[2] = make_float2(v23.x, v23.y); v[3] = make_float2(v23.z, v23.w);
+                } else {
+                    v[0] = s_v[i];
+                }
 #pragma unroll
                 for (int s = 0; s < NPOL; ++s)
 #pragma unroll
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(256) degrid_warp_kernel(DegridArgs a) {
         }
         const int S = a.bin_support[r.bin];
         const int L = S * S;
-        const int64_t kbase = a.bin_offset[r.bin] + (int64_t)(r.fy * a.OS + r.fx) * L * P;
+        const int64_t kbase = a.bin_offset[r.bin] + (int64_t)(r.fy * a.OS + r.fx) * L * P;  // block start
         const float2 *g0 = a.grid + (int64_t)r.y0 * a.N + r.x0;
         const int64_t plane = (int64_t)a.N * a.N;
         float2 acc[NPOL];
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(256) degrid_warp_kernel(DegridArgs a) {
         int jy = lane / S, jx = lane - jy * S;
         for (int t = lane; t < L; t += 32) {
             float2 k[P];
-            load_k<ST, P>(a.ktab, kbase + (int64_t)t * P, k);
+            load_k<ST, P>(a.ktab, kbase, L, t, k);
             const float2 *gp = g0 + (int64_t)jy * a.N + jx;
             float2 gv[NPOL];
 #pragma unroll

@@ -64,6 +64,8 @@ struct aw_kernel_set {
     std::vector<int64_t> bin_offset;  // element offset of each bin (complex elements)
     int64_t total_elems = 0;
     int elem_bytes = 8;
+    // complex values per 16-byte chunk of the table layout (see aw_tab_index)
+    int ce = 1;
     void *d_table = nullptr;
     int32_t *d_bin_support = nullptr;
     int64_t *d_bin_offset = nullptr;
@@ -108,6 +110,16 @@ struct aw_plan {
     cudaStream_t g_stream = nullptr;
 };
 
+// ---------------------------------------------------------------- table layout
+// Inside one (bin, fy, fx) block of L = S*S taps, the P Mueller values of a tap
+// are split into 16-byte chunks of `ce` complex values (ce = 2 for FP32, 4 for
+// 16-bit storage, or P if P is smaller) and stored chunk-major, tap-minor:
+// index(tap, m) = ((m / ce) * L + tap) * ce + m % ce.  Threads that handle
+// consecutive taps then read consecutive 16-byte words (coalesced loads).
+__host__ __device__ inline int64_t aw_tab_index(int ce, int64_t L, int64_t tap, int m) {
+    return ((int64_t)(m / ce) * L + tap) * ce + (m % ce);
+}
+
 // ---------------------------------------------------------------- helpers
 int aw_ctx_fft_plan(aw_ctx *ctx, int rank_tag, int n, int batch, cufftType type, cufftHandle *out);
 int aw_ctx_gridcorr(aw_ctx *ctx, int N, double W, float **out);
@@ -141,7 +153,8 @@ int aw_launch_degrid(const aw_plan *plan, const aw_kernel_set *kset, const void 
                      void *vis_out, cudaStream_t stream);
 
 // Storage conversion (aw_synth.cu).
-int aw_convert_table(const float2 *src, void *dst, int64_t n, int storage, cudaStream_t s);
-int aw_export_table(const void *src, float2 *dst, int64_t n, int storage, float inv_scale, cudaStream_t s);
-int aw_convert_table_scaled(const float2 *src, void *dst, int64_t n, int storage, float scale, cudaStream_t s);
+int aw_export_table(const void *src, float2 *dst, int64_t nblocks, int L, int P, int ce, int storage,
+                    float inv_scale, cudaStream_t s);
+int aw_convert_table_scaled(const float2 *src, void *dst, int64_t nblocks, int L, int P, int ce, int storage,
+                            float scale, cudaStream_t s);
 int aw_table_absmax(const float2 *src, int64_t n, float *out_host, cudaStream_t s);

@@ -314,11 +314,13 @@ __device__ __forceinline__ void store_elem<AW_STORAGE_FP16>(void *dst, int64_t i
     reinterpret_cast<__half2 *>(dst)[i] = v;
 }
 
-// Cut S x S taps at OS x OS fine offsets out of the transformed buffers.
+// Cut S x S taps at OS x OS fine offsets out of the transformed buffers and
+// store them in the chunked table layout (aw_tab_index).
 template <int STORAGE>
-__global__ void synth_extract_kernel(const cufftDoubleComplex *Z, int MO, int S, int OS, int P,
+__global__ void synth_extract_kernel(const cufftDoubleComplex *Z, int MO, int S, int OS, int P, int ce,
                                      double scale, void *dst) {
-    const int64_t total = (int64_t)OS * OS * S * S * P;
+    const int64_t L = (int64_t)S * S;
+    const int64_t total = (int64_t)OS * OS * L * P;
     const int rho = (S - 2) * OS / 2;
     const size_t plane = (size_t)MO * MO;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -334,34 +336,37 @@ __global__ void synth_extract_kernel(const cufftDoubleComplex *Z, int MO, int S,
         const int iy = ((ky % MO) + MO) % MO;
         const int ix = ((kx % MO) + MO) % MO;
         const cufftDoubleComplex z = Z[(size_t)m * plane + (size_t)iy * MO + ix];
-        store_elem<STORAGE>(dst, i, z.x * scale, z.y * scale);
+        const int64_t o = ((int64_t)fy * OS + fx) * L * P + aw_tab_index(ce, L, (int64_t)jy * S + jx, m);
+        store_elem<STORAGE>(dst, o, z.x * scale, z.y * scale);
+    }
+}
+
+// canonical [blocks][L][P] complex64 <-> chunked storage layout
+template <int STORAGE>
+__global__ void convert_kernel(const float2 *src, void *dst, int64_t n, int L, int P, int ce, float scale) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i % P);
+        const int64_t tap = (i / P) % L;
+        const int64_t blk = i / ((int64_t)P * L);
+        const int64_t o = blk * L * P + aw_tab_index(ce, L, tap, m);
+        store_elem<STORAGE>(dst, o, (double)(src[i].x * scale), (double)(src[i].y * scale));
     }
 }
 
 template <int STORAGE>
-__global__ void convert_kernel(const float2 *src, void *dst, int64_t n, float scale) {
+__global__ void export_kernel(const void *src, float2 *dst, int64_t n, int L, int P, int ce, float inv_scale) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = make_float2(src[i].x * scale, src[i].y * scale);
-        if (STORAGE == AW_STORAGE_FP32) {
-            reinterpret_cast<float2 *>(dst)[i] = v;
-        } else if (STORAGE == AW_STORAGE_BF16) {
-            reinterpret_cast<__nv_bfloat162 *>(dst)[i] = __floats2bfloat162_rn(v.x, v.y);
-        } else {
-            reinterpret_cast<__half2 *>(dst)[i] = __floats2half2_rn(v.x, v.y);
-        }
-    }
-}
-
-template <int STORAGE>
-__global__ void export_kernel(const void *src, float2 *dst, int64_t n, float inv_scale) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i % P);
+        const int64_t tap = (i / P) % L;
+        const int64_t blk = i / ((int64_t)P * L);
+        const int64_t o = blk * L * P + aw_tab_index(ce, L, tap, m);
         float2 v;
         if (STORAGE == AW_STORAGE_FP32) {
-            v = reinterpret_cast<const float2 *>(src)[i];
+            v = reinterpret_cast<const float2 *>(src)[o];
         } else if (STORAGE == AW_STORAGE_BF16) {
-            v = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(src)[i]);
+            v = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(src)[o]);
         } else {
-            v = __half22float2(reinterpret_cast<const __half2 *>(src)[i]);
+            v = __half22float2(reinterpret_cast<const __half2 *>(src)[o]);
         }
         dst[i] = make_float2(v.x * inv_scale, v.y * inv_scale);
     }
@@ -382,24 +387,24 @@ static int blocks_for(int64_t n, int threads, int cap = 65535 * 4) {
     return (int)b;
 }
 
-int aw_convert_table_scaled(const float2 *src, void *dst, int64_t n, int storage, float scale, cudaStream_t s) {
+int aw_convert_table_scaled(const float2 *src, void *dst, int64_t nblocks, int L, int P, int ce, int storage,
+                            float scale, cudaStream_t s) {
+    const int64_t n = nblocks * L * P;
     const int nb = blocks_for(n, 256);
-    if (storage == AW_STORAGE_FP32) convert_kernel<AW_STORAGE_FP32><<<nb, 256, 0, s>>>(src, dst, n, scale);
-    else if (storage == AW_STORAGE_BF16) convert_kernel<AW_STORAGE_BF16><<<nb, 256, 0, s>>>(src, dst, n, scale);
-    else convert_kernel<AW_STORAGE_FP16><<<nb, 256, 0, s>>>(src, dst, n, scale);
+    if (storage == AW_STORAGE_FP32) convert_kernel<AW_STORAGE_FP32><<<nb, 256, 0, s>>>(src, dst, n, L, P, ce, scale);
+    else if (storage == AW_STORAGE_BF16) convert_kernel<AW_STORAGE_BF16><<<nb, 256, 0, s>>>(src, dst, n, L, P, ce, scale);
+    else convert_kernel<AW_STORAGE_FP16><<<nb, 256, 0, s>>>(src, dst, n, L, P, ce, scale);
     AW_CHECK_LAUNCH();
     return AW_OK;
 }
 
-int aw_convert_table(const float2 *src, void *dst, int64_t n, int storage, cudaStream_t s) {
-    return aw_convert_table_scaled(src, dst, n, storage, 1.0f, s);
-}
-
-int aw_export_table(const void *src, float2 *dst, int64_t n, int storage, float inv_scale, cudaStream_t s) {
+int aw_export_table(const void *src, float2 *dst, int64_t nblocks, int L, int P, int ce, int storage,
+                    float inv_scale, cudaStream_t s) {
+    const int64_t n = nblocks * L * P;
     const int nb = blocks_for(n, 256);
-    if (storage == AW_STORAGE_FP32) export_kernel<AW_STORAGE_FP32><<<nb, 256, 0, s>>>(src, dst, n, inv_scale);
-    else if (storage == AW_STORAGE_BF16) export_kernel<AW_STORAGE_BF16><<<nb, 256, 0, s>>>(src, dst, n, inv_scale);
-    else export_kernel<AW_STORAGE_FP16><<<nb, 256, 0, s>>>(src, dst, n, inv_scale);
+    if (storage == AW_STORAGE_FP32) export_kernel<AW_STORAGE_FP32><<<nb, 256, 0, s>>>(src, dst, n, L, P, ce, inv_scale);
+    else if (storage == AW_STORAGE_BF16) export_kernel<AW_STORAGE_BF16><<<nb, 256, 0, s>>>(src, dst, n, L, P, ce, inv_scale);
+    else export_kernel<AW_STORAGE_FP16><<<nb, 256, 0, s>>>(src, dst, n, L, P, ce, inv_scale);
     AW_CHECK_LAUNCH();
     return AW_OK;
 }
@@ -482,6 +487,7 @@ int aw_kernel_set_geometry(const aw_kernel_spec *spec, aw_kernel_set *ks) {
     }
     ks->total_elems = pos;
     ks->elem_bytes = spec->storage == AW_STORAGE_FP32 ? 8 : 4;
+    ks->ce = std::min(ks->P, 16 / ks->elem_bytes);
     return AW_OK;
 }
 
@@ -581,11 +587,11 @@ int aw_synthesise(aw_ctx *ctx, aw_kernel_set *ks, cudaStream_t s) {
                 char *dst = static_cast<char *>(ks->d_table) + ks->bin_offset[b] * ks->elem_bytes;
                 const int nb = blocks_for(n, 256);
                 if (sp.storage == AW_STORAGE_FP32)
-                    synth_extract_kernel<AW_STORAGE_FP32><<<nb, 256, 0, s>>>(Z, MO, S, OS, P, scale, dst);
+                    synth_extract_kernel<AW_STORAGE_FP32><<<nb, 256, 0, s>>>(Z, MO, S, OS, P, ks->ce, scale, dst);
                 else if (sp.storage == AW_STORAGE_BF16)
-                    synth_extract_kernel<AW_STORAGE_BF16><<<nb, 256, 0, s>>>(Z, MO, S, OS, P, scale, dst);
+                    synth_extract_kernel<AW_STORAGE_BF16><<<nb, 256, 0, s>>>(Z, MO, S, OS, P, ks->ce, scale, dst);
                 else
-                    synth_extract_kernel<AW_STORAGE_FP16><<<nb, 256, 0, s>>>(Z, MO, S, OS, P, scale, dst);
+                    synth_extract_kernel<AW_STORAGE_FP16><<<nb, 256, 0, s>>>(Z, MO, S, OS, P, ks->ce, scale, dst);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) { rc = aw_set_error(AW_ECUDA, "extract: %s", cudaGetErrorString(e)); break; }
             }
