@@ -1,0 +1,104 @@
+"""FP64 oracle of the learned kernel surrogate: a SIREN-style coordinate MLP.
+
+TEST INFRASTRUCTURE ONLY.  The surrogate maps continuous kernel coordinates
+to the P complex Mueller kernel values of one tap, standing in for the
+per-bin FFT synthesis of Sec. 3.2 (the kernels it learns are the uv
+transforms of the Mueller cells times the anti-aliasing function and the w
+term).  Definitions shared with the CUDA path (written separately there):
+
+* features (5): x = [d_u / D, d_v / D, 2 w / w_max - 1, (f - f_c) / f_h,
+  (chi - chi_c) / chi_h], with (d_u, d_v) the grid-minus-visibility offset of
+  the tap in cells;
+* layers: sizes [5, H, H, H, H, 2P]; the first four apply
+  h = sin(omega0 * (W h_prev + b)), the last is linear;
+* parameters: one flat vector, per layer W [out][in] row-major then b [out];
+* loss: L = (1/B) sum_b sum_j (y_bj - t_bj)^2;
+* Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+  p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+
+Pinned by central finite differences in tests/test_oracle_mlp.py.
+"""
+from __future__ import annotations
+
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+
+def layer_sizes(n_in: int = 5, width: int = 128, n_hidden: int = 4, P: int = 16) -> List[int]:
+    return [n_in] + [width] * n_hidden + [2 * P]
+
+
+def n_params(sizes: Sequence[int]) -> int:
+    return sum(sizes[i + 1] * sizes[i] + sizes[i + 1] for i in range(len(sizes) - 1))
+
+
+def unpack(params: np.ndarray, sizes: Sequence[int]) -> List[Tuple[np.ndarray, np.ndarray]]:
+    out, pos = [], 0
+    for i in range(len(sizes) - 1):
+        n_in, n_out = sizes[i], sizes[i + 1]
+        W = params[pos:pos + n_out * n_in].reshape(n_out, n_in)
+        pos += n_out * n_in
+        b = params[pos:pos + n_out]
+        pos += n_out
+        out.append((W, b))
+    return out
+
+
+def forward(params: np.ndarray, sizes: Sequence[int], X: np.ndarray, omega0: float):
+    """Returns (Y [B][2P], cache of pre-activations and activations)."""
+    layers = unpack(np.asarray(params, np.float64), sizes)
+    h = np.asarray(X, np.float64)
+    acts, pres = [h], []
+    for li, (W, b) in enumerate(layers):
+        z = h @ W.T + b
+        pres.append(z)
+        if li < len(layers) - 1:
+            h = np.sin(omega0 * z)
+        else:
+            h = z
+        acts.append(h)
+    return h, (acts, pres)
+
+
+def loss(Y: np.ndarray, T: np.ndarray) -> float:
+    return float(np.sum((Y - T) ** 2) / Y.shape[0])
+
+
+def backward(params: np.ndarray, sizes: Sequence[int], cache, Y: np.ndarray, T: np.ndarray,
+             omega0: float) -> np.ndarray:
+    """Analytic gradient of loss(Y, T) with respect to the flat parameters."""
+    layers = unpack(np.asarray(params, np.float64), sizes)
+    acts, pres = cache
+    B = Y.shape[0]
+    grads = []
+    dz = 2.0 * (Y - T) / B
+    for li in range(len(layers) - 1, -1, -1):
+        W, b = layers[li]
+        h_prev = acts[li]
+        dW = dz.T @ h_prev
+        db = dz.sum(axis=0)
+        grads.append((dW, db))
+        if li > 0:
+            dh = dz @ W
+            dz = dh * omega0 * np.cos(omega0 * pres[li - 1])
+    flat = []
+    for dW, db in reversed(grads):
+        flat.append(dW.reshape(-1))
+        flat.append(db)
+    return np.concatenate(flat)
+
+
+def adam_step(params, grads, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
+              eps: float = 1e-8):
+    m = b1 * m + (1 - b1) * grads
+    v = b2 * v + (1 - b2) * grads * grads
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return params - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def features(du, dv, w, f, chi, D, w_max, f_c, f_h, chi_c, chi_h) -> np.ndarray:
+    du = np.asarray(du, np.float64)
+    return np.stack([du / D, np.asarray(dv) / D, 2.0 * np.asarray(w) / w_max - 1.0,
+                     (np.asarray(f) - f_c) / f_h, (np.asarray(chi) - chi_c) / chi_h], axis=-1)
