@@ -299,6 +299,76 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset, 
 int aw_fft_to_image(aw_ctx *ctx, const aw_kernel_set *kset, void *grid, double weight_sum,
                     float *image, void *stream);
 
+/* ---- learned kernel surrogate --------------------------------------------- */
+/*
+ * A SIREN-style coordinate MLP standing in for the per-bin FFT kernel
+ * synthesis of Sec. 3.2: it maps the continuous coordinates of a tap
+ * (grid-minus-visibility offset d_u, d_v in cells, w in wavelengths,
+ * frequency, parallactic angle) to the npol^2 complex Mueller kernel values
+ * of that tap, and is trained on tables built by aw_make_kernels.
+ *   features x = [d_u/D, d_v/D, 2 w/w_max - 1, (f - f_c)/f_h, (chi - chi_c)/chi_h]
+ *   layers [5, width x n_hidden, 2 npol^2]; hidden h = sin(omega0 (W h + b)),
+ *   linear output; kernel value = output * out_scale.
+ *   Parameters: one flat FP32 vector, per layer W [out][in] then b [out].
+ *   Loss (1/B) sum (y - t)^2; Adam (b1 0.9, b2 0.999, eps 1e-8) with bias
+ *   correction and a cosine learning-rate decay from lr to lr_final.
+ * Training runs in the library's kernels with FP32 master weights; the
+ * inline evaluation uses an FP16 copy of the weights with FP32 accumulation.
+ */
+typedef struct aw_surrogate_cfg {
+    int32_t npol;            /* 1 or 4                                           */
+    int32_t width;           /* hidden width (128)                               */
+    int32_t n_hidden;        /* number of sine layers (4)                        */
+    float omega0;            /* SIREN frequency (30)                             */
+    double D, w_max, f_c, f_h, chi_c, chi_h;  /* feature scales (see above)      */
+    float out_scale;         /* kernel value = output * out_scale                */
+    uint64_t seed;           /* initialisation seed                              */
+} aw_surrogate_cfg;
+
+typedef struct aw_train_cfg {
+    int32_t steps;           /* Adam steps                                        */
+    int32_t batch;           /* points per step (sampled from the exact tables)   */
+    float lr, lr_final;      /* cosine decay from lr to lr_final                  */
+    uint64_t seed;           /* sampling seed (SplitMix64 counters)               */
+} aw_train_cfg;
+
+typedef struct aw_train_report {
+    float loss_first;        /* loss of the first step                            */
+    float loss_last;         /* mean loss over the last 5 % of steps              */
+    int32_t steps;
+    double seconds;          /* wall time of the training loop                    */
+} aw_train_report;
+
+int aw_surrogate_create(aw_ctx *ctx, const aw_surrogate_cfg *cfg, aw_surrogate **out);
+int aw_surrogate_destroy(aw_surrogate *sur);
+int aw_surrogate_nparams(const aw_surrogate *sur, int64_t *n);
+/* Copy parameters from / to host memory ([nparams] FP32).  set_params also
+ * resets the Adam state. */
+int aw_surrogate_set_params(aw_surrogate *sur, const float *host_params);
+int aw_surrogate_get_params(const aw_surrogate *sur, float *host_params);
+/* Forward pass on B feature rows: X device float [B][5] -> Y device float
+ * [B][2 npol^2] (FP32 weights). */
+int aw_surrogate_forward(aw_ctx *ctx, aw_surrogate *sur, const float *X, int32_t B, float *Y, void *stream);
+/* Loss and gradient on one batch (targets T device float [B][2 npol^2]):
+ * *loss (host) and grad (device float [nparams]).  Synchronises `stream`. */
+int aw_surrogate_loss_grad(aw_ctx *ctx, aw_surrogate *sur, const float *X, const float *T, int32_t B,
+                           double *loss, float *grad, void *stream);
+/* Train on random (bin, fine offset, tap) points of `exact` (its role and
+ * npol must match the surrogate).  Synchronises `stream`. */
+int aw_surrogate_train(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exact, const aw_train_cfg *cfg,
+                       aw_train_report *report, void *stream);
+/*
+ * aw_surrogate_tables - evaluate the surrogate at every table point of
+ * `exact` into a new set with the same geometry (`storage` must equal the
+ * exact set's storage, else AW_EUNSUPPORTED).  Per w
+ * plane, if the relative L2 error of any of its bins exceeds reject_rel the
+ * plane keeps the exact tables (fallback; info.n_rejected counts those bins,
+ * and the call returns AW_EREJECTED if any).  bin_err (host [nbins], may be
+ * NULL) receives each bin's relative L2 error.  Synchronises `stream`.
+ */
+int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exact, float reject_rel,
+                        int32_t storage, aw_kernel_set **out, float *bin_err, void *stream);
+
 /* ---- mosaic weighting (Sec. 2.2, Eq. 1) ------------------------------------- */
 
 /*

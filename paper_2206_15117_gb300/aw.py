@@ -79,7 +79,32 @@ SIGNATURES = {
     "aw_fft_to_image": (ctypes.c_int, [c_p, c_p, c_p, c_dbl, c_p, c_p]),
     "mosaic_gamma": (ctypes.c_int, [c_p, c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
+    "aw_surrogate_create": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(c_p)]),
+    "aw_surrogate_destroy": (ctypes.c_int, [c_p]),
+    "aw_surrogate_nparams": (ctypes.c_int, [c_p, ctypes.POINTER(c_i64)]),
+    "aw_surrogate_set_params": (ctypes.c_int, [c_p, c_p]),
+    "aw_surrogate_get_params": (ctypes.c_int, [c_p, c_p]),
+    "aw_surrogate_forward": (ctypes.c_int, [c_p, c_p, c_p, c_i32, c_p, c_p]),
+    "aw_surrogate_loss_grad": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_i32, ctypes.POINTER(c_dbl), c_p, c_p]),
+    "aw_surrogate_train": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p]),
+    "aw_surrogate_tables": (ctypes.c_int, [c_p, c_p, c_p, ctypes.c_float, c_i32, ctypes.POINTER(c_p), c_p, c_p]),
 }
+
+
+class aw_surrogate_cfg(ctypes.Structure):
+    _fields_ = [("npol", c_i32), ("width", c_i32), ("n_hidden", c_i32), ("omega0", ctypes.c_float),
+                ("D", c_dbl), ("w_max", c_dbl), ("f_c", c_dbl), ("f_h", c_dbl), ("chi_c", c_dbl),
+                ("chi_h", c_dbl), ("out_scale", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class aw_train_cfg(ctypes.Structure):
+    _fields_ = [("steps", c_i32), ("batch", c_i32), ("lr", ctypes.c_float), ("lr_final", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class aw_train_report(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float), ("steps", c_i32),
+                ("seconds", c_dbl)]
 
 _lib = None
 
@@ -333,3 +358,71 @@ def device_observation(ob, device="cuda:0", flags=None):
     d = vis_desc(tens["uvw"], tens["row"], tens["chan"], tens["freq"], tens["pa_bin"], tens["fbin"],
                  tens["flags"])
     return d, tens
+
+
+# ---------------------------------------------------------------- learned surrogate
+def aw_surrogate_create(ctx: Handle, npol: int = 4, width: int = 128, n_hidden: int = 4, omega0: float = 30.0,
+                        D: float = 33.0, w_max: float = 1.0, f_c: float = 1.35e9, f_h: float = 0.15e9,
+                        chi_c: float = 0.0, chi_h: float = 1.5, out_scale: float = 0.02, seed: int = 1) -> Handle:
+    c = aw_surrogate_cfg(int(npol), int(width), int(n_hidden), float(omega0), float(D), float(w_max),
+                         float(f_c), float(f_h), float(chi_c), float(chi_h), float(out_scale), int(seed))
+    out = c_p()
+    _check(load().aw_surrogate_create(ctx.ptr, ctypes.byref(c), ctypes.byref(out)), "aw_surrogate_create")
+    h = Handle(out, "aw_surrogate_destroy")
+    h.cfg = c
+    return h
+
+
+def aw_surrogate_nparams(sur: Handle) -> int:
+    n = c_i64()
+    _check(load().aw_surrogate_nparams(sur.ptr, ctypes.byref(n)), "aw_surrogate_nparams")
+    return int(n.value)
+
+
+def aw_surrogate_set_params(sur: Handle, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().aw_surrogate_set_params(sur.ptr, p.ctypes.data), "aw_surrogate_set_params")
+
+
+def aw_surrogate_get_params(sur: Handle):
+    import numpy as np
+    p = np.empty(aw_surrogate_nparams(sur), dtype=np.float32)
+    _check(load().aw_surrogate_get_params(sur.ptr, p.ctypes.data), "aw_surrogate_get_params")
+    return p
+
+
+def aw_surrogate_forward(ctx: Handle, sur: Handle, X, Y, stream=None):
+    _check(load().aw_surrogate_forward(ctx.ptr, sur.ptr, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)),
+           "aw_surrogate_forward")
+
+
+def aw_surrogate_loss_grad(ctx: Handle, sur: Handle, X, T, grad, stream=None) -> float:
+    loss = c_dbl()
+    _check(load().aw_surrogate_loss_grad(ctx.ptr, sur.ptr, _ptr(X), _ptr(T), int(X.shape[0]), ctypes.byref(loss),
+                                         _ptr(grad), _stream(stream)), "aw_surrogate_loss_grad")
+    return float(loss.value)
+
+
+def aw_surrogate_train(ctx: Handle, sur: Handle, exact: Handle, steps: int = 2000, batch: int = 65536,
+                       lr: float = 1e-3, lr_final: float = 1e-5, seed: int = 7, stream=None) -> aw_train_report:
+    c = aw_train_cfg(int(steps), int(batch), float(lr), float(lr_final), int(seed))
+    rep = aw_train_report()
+    _check(load().aw_surrogate_train(ctx.ptr, sur.ptr, exact.ptr, ctypes.byref(c), ctypes.byref(rep),
+                                     _stream(stream)), "aw_surrogate_train")
+    return rep
+
+
+def aw_surrogate_tables(ctx: Handle, sur: Handle, exact: Handle, reject_rel: float, storage: int = AW_STORAGE_FP32,
+                        stream=None):
+    """Returns (kernel set handle, per-bin relative L2 errors, n_rejected bins)."""
+    import numpy as np
+    nb = aw_kernel_set_info(exact).nbins
+    err = np.zeros(nb, dtype=np.float32)
+    out = c_p()
+    rc = load().aw_surrogate_tables(ctx.ptr, sur.ptr, exact.ptr, ctypes.c_float(reject_rel), int(storage),
+                                    ctypes.byref(out), err.ctypes.data, _stream(stream))
+    if rc not in (AW_OK, AW_EREJECTED):
+        _check(rc, "aw_surrogate_tables")
+    ks = Handle(out, "aw_kernel_set_destroy")
+    return ks, err, aw_kernel_set_info(ks).n_rejected
