@@ -369,6 +369,23 @@ int aw_surrogate_train(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exac
 int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exact, float reject_rel,
                         int32_t storage, aw_kernel_set **out, float *bin_err, void *stream);
 
+/*
+ * aw_grid_learned - gridding with the surrogate evaluated inline (no kernel
+ * tables): for every visibility and tap of its footprint the MLP runs on
+ * tensor cores (mma.sync, FP16 weights and activations, FP32 accumulation)
+ * at the tap's exact offset from the visibility (no oversampling grid), the
+ * visibility's exact |w| (no w-plane quantisation), its channel frequency
+ * and its parallactic-angle bin centre; the P kernel values are applied as
+ * in aw_grid (same flip, weights, skip rules, accumulation into `grid`).
+ * The plan gives the footprints (supports per w plane) and the order.  W
+ * planes rejected by the last aw_surrogate_tables call use `fallback` (the
+ * exact set) at the plan's quantised offsets.  The surrogate must have width
+ * 128 and 4 sine layers (AW_EUNSUPPORTED otherwise).  The plan's visibility
+ * descriptor arrays are read again and must still be valid.
+ */
+int aw_grid_learned(aw_ctx *ctx, const aw_plan *plan, aw_surrogate *sur, const aw_kernel_set *fallback,
+                    const void *vis, const float *weight, void *grid, aw_stats *stats, void *stream);
+
 /* ---- mosaic weighting (Sec. 2.2, Eq. 1) ------------------------------------- */
 
 /*

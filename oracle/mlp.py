@@ -102,3 +102,63 @@ def features(du, dv, w, f, chi, D, w_max, f_c, f_h, chi_c, chi_h) -> np.ndarray:
     du = np.asarray(du, np.float64)
     return np.stack([du / D, np.asarray(dv) / D, 2.0 * np.asarray(w) / w_max - 1.0,
                      (np.asarray(f) - f_c) / f_h, (np.asarray(chi) - chi_c) / chi_h], axis=-1)
+
+
+def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co, vis, weight=None,
+                fp16_layers=True):
+    """Gridding with the surrogate evaluated at every (visibility, tap) point.
+
+    For each gridded visibility (footprint x0, y0 and flip from the oracle's
+    coordinate step) the tap (jy, jx) lies at d = (x0 + jx) - X cells from the
+    visibility's exact position X = u N dl + N/2 (no oversampling grid); the
+    features use its exact |w|, its channel frequency and the centre of its
+    parallactic-angle bin; the network's 2P outputs times out_scale are the
+    Mueller kernel values K_{s,c}, and G[s][y][x] += sum_c K_{s,c} w'_c V'_c.
+    With fp16_layers the weights of the tensor-core layers (all but the first)
+    are rounded to FP16, as the GPU stores them.
+    `scales` = (D, w_max, f_c, f_h, chi_c, chi_h, out_scale).
+    """
+    from . import core as oc
+    D, w_max, f_c, f_h, chi_c, chi_h, out_scale = scales
+    p = np.array(params, np.float64)
+    if fp16_layers:
+        layers = unpack(p, sizes)
+        pos = sizes[0] * sizes[1] + sizes[1]
+        for li in range(1, len(sizes) - 1):
+            n_in, n_out = sizes[li], sizes[li + 1]
+            p[pos:pos + n_out * n_in] = p[pos:pos + n_out * n_in].astype(np.float16).astype(np.float64)
+            pos += n_out * n_in + n_out
+    npol = spec.npol
+    N = spec.N
+    G = np.zeros((npol, N, N), np.complex128)
+    v = np.asarray(vis, np.complex128).reshape(-1, npol)
+    w = np.ones(v.shape, np.float64) if weight is None else np.asarray(weight, np.float64).reshape(-1, npol)
+    f = np.asarray(freq, np.float64)[chan_of_vis] / oc.C_LIGHT
+    uvwl = np.asarray(uvw, np.float64)[row_of_vis] * f[:, None]
+    for k in np.flatnonzero(co.valid == 1):
+        vk, wk = v[k].copy(), w[k].copy()
+        u, vv, ww = uvwl[k]
+        if co.flip[k]:
+            u, vv, ww = -u, -vv, -ww
+            vk = np.conj(vk)
+            if npol == 4:
+                vk = vk[[0, 2, 1, 3]]
+                wk = wk[[0, 2, 1, 3]]
+        X = u * (N * spec.dl) + N // 2
+        Y = vv * (N * spec.dl) + N // 2
+        b = co.bin[k]
+        pidx = b // (spec.npa * spec.nfb)
+        a = (b // spec.nfb) % spec.npa
+        S = spec.supports[pidx]
+        jy, jx = np.meshgrid(np.arange(S), np.arange(S), indexing="ij")
+        du = (co.x0[k] + jx.ravel()) - X
+        dv = (co.y0[k] + jy.ravel()) - Y
+        nf = du.size
+        Xf = features(du, dv, np.full(nf, ww), np.full(nf, freq[chan_of_vis[k]]), np.full(nf, spec.pa[a]),
+                      D, w_max, f_c, f_h, chi_c, chi_h)
+        out, _ = forward(p, sizes, Xf, omega0)
+        K = (out[:, 0::2] + 1j * out[:, 1::2]) * out_scale          # [taps][P]
+        K = K.reshape(S, S, npol, npol)                              # [jy][jx][s][c]
+        contrib = np.einsum("yxsc,c->syx", K, wk * vk)
+        G[:, co.y0[k]:co.y0[k] + S, co.x0[k]:co.x0[k] + S] += contrib
+    return G

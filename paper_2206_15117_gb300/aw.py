@@ -88,6 +88,7 @@ SIGNATURES = {
     "aw_surrogate_loss_grad": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_i32, ctypes.POINTER(c_dbl), c_p, c_p]),
     "aw_surrogate_train": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_tables": (ctypes.c_int, [c_p, c_p, c_p, ctypes.c_float, c_i32, ctypes.POINTER(c_p), c_p, c_p]),
+    "aw_grid_learned": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, ctypes.POINTER(aw_stats), c_p]),
 }
 
 
@@ -426,3 +427,11 @@ def aw_surrogate_tables(ctx: Handle, sur: Handle, exact: Handle, reject_rel: flo
         _check(rc, "aw_surrogate_tables")
     ks = Handle(out, "aw_kernel_set_destroy")
     return ks, err, aw_kernel_set_info(ks).n_rejected
+
+
+def aw_grid_learned(ctx: Handle, plan: Handle, sur: Handle, fallback: Handle, vis, weight, grid,
+                    want_stats: bool = False, stream=None) -> Optional[aw_stats]:
+    st = aw_stats() if want_stats else None
+    _check(load().aw_grid_learned(ctx.ptr, plan.ptr, sur.ptr, fallback.ptr, _ptr(vis), _ptr(weight), _ptr(grid),
+                                  ctypes.byref(st) if st is not None else None, _stream(stream)), "aw_grid_learned")
+    return st

@@ -1,0 +1,429 @@
+// Gridding with the learned surrogate evaluated inline: every (visibility,
+// tap) point runs the SIREN MLP on tensor cores (mma.sync m16n8k16, FP16
+// weights and activations, FP32 accumulation) to produce the P complex
+// Mueller kernel values of that tap, which are applied to the visibility and
+// added to the grid.  The kernel coordinates are continuous: the exact
+// visibility position (no oversampling grid), its exact w (no w-plane
+// quantisation) and its channel frequency; no kernel table is read.  Items
+// whose w plane the surrogate was rejected on read the exact tables instead
+// (the same accumulation code, fed from memory).
+//
+// Sec. 3.2 of arXiv:2206.15117: the gridding kernels are the uv transforms of
+// the inverse Mueller cells; here a network trained on those transforms
+// supplies them.
+#include <algorithm>
+#include <cmath>
+
+#include "aw_internal.h"
+#include "aw_mlp.h"
+
+namespace {
+
+constexpr int LW = 128;        // hidden width
+constexpr int LPAD = LW + 8;   // shared-memory row stride in halves (bank-conflict free ldmatrix)
+constexpr int LWARPS = 8;
+constexpr int LCHUNK = 128;    // staged visibilities per pass over an item
+
+struct __align__(16) VisL {
+    float2 v[4];     // flipped, weighted values
+    float dx, dy;    // exact position minus footprint start, cells
+    float w, f;      // |w| (wavelengths) and frequency (Hz)
+    int pos;         // x0 | y0 << 16
+    int koff;        // fallback table block offset (fy * OS + fx) * L * P
+    int pad0, pad1;
+};
+
+struct LearnArgs {
+    const aw_rec *rec;
+    const int4 *items;
+    int64_t nitems;
+    const float2 *vis;
+    const float *weight;
+    float2 *grid;
+    int N, OS;
+    // coordinates for the exact positions
+    const double *uvw;
+    const uint32_t *row;
+    const uint16_t *chan;
+    const double *freq;
+    double cells_per_lambda, half_cells;
+    const int32_t *bin_support;
+    int npa, nfb;
+    const double *pa_centres;
+    // surrogate
+    const __half *Wh;
+    const float *Wf;
+    int64_t woff[5], boff[5];
+    float omega0, inv_D, w_scale, f_c, inv_f_h, chi_c, inv_chi_h, out_scale;
+    const uint8_t *plane_rejected;
+    // exact fallback tables
+    const void *ktab;
+    const int64_t *bin_offset;
+    int storage, ce;
+    float inv_kscale;
+    // statistics / queue
+    double *wsum;
+    unsigned long long *nonfinite;
+    unsigned int *counter;
+};
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float2 read_tab(const void *tab, int storage, int64_t idx) {
+    if (storage == AW_STORAGE_FP32) return reinterpret_cast<const float2 *>(tab)[idx];
+    if (storage == AW_STORAGE_BF16) return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(tab)[idx]);
+    return __half22float2(reinterpret_cast<const __half2 *>(tab)[idx]);
+}
+
+// One 128 -> NT*8 layer for the warp's 16 rows: out = act(A W^T + b).
+template <int NT>
+__device__ __forceinline__ void warp_layer(const __half *sAin, const __half *sWl, const float *bias, float (&acc)[NT][4],
+                                           int lane) {
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < LW / 16; ++ks) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(a0, a1, a2, a3, sAin + (lane % 16) * LPAD + ks * 16 + (lane / 16) * 8);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            uint32_t b0, b1;
+            ldsm_x2(b0, b1, sWl + (nt * 8 + (lane % 8)) * LPAD + ks * 16 + ((lane / 8) % 2) * 8);
+            mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        }
+    }
+    const int tig = lane % 4;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const float b0 = bias[nt * 8 + tig * 2], b1 = bias[nt * 8 + tig * 2 + 1];
+        acc[nt][0] += b0;
+        acc[nt][1] += b1;
+        acc[nt][2] += b0;
+        acc[nt][3] += b1;
+    }
+}
+
+template <int NPOL>
+__global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
+    constexpr int P = NPOL * NPOL;
+    constexpr int NOUT = (2 * P + 7) / 8 * 8;   // 32 (full pol) or 8 (Stokes I)
+    constexpr int NTO = NOUT / 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __half *sW = reinterpret_cast<__half *>(smem);             // [3][LW][LPAD]
+    __half *sWo = sW + 3 * LW * LPAD;                           // [NOUT][LPAD]
+    __half *sAct = sWo + NOUT * LPAD;                           // [LWARPS][2][16][LPAD]
+    float *sW1 = reinterpret_cast<float *>(sAct + LWARPS * 2 * 16 * LPAD);  // [LW][5]
+    float *sB = sW1 + LW * 5;                                   // [4][LW] hidden biases, then [NOUT]
+    VisL *sv = reinterpret_cast<VisL *>(sB + 4 * LW + NOUT);    // [LCHUNK]
+    __shared__ int s_item, s_cnt;
+    __shared__ double s_red[LWARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---- weights into shared memory once
+    for (int l = 0; l < 3; ++l)
+        for (int i = tid; i < LW * LW; i += blockDim.x) {
+            const int o = i / LW, k = i % LW;
+            sW[(l * LW + o) * LPAD + k] = a.Wh[a.woff[l + 1] + i];
+        }
+    for (int i = tid; i < NOUT * LW; i += blockDim.x) {
+        const int o = i / LW, k = i % LW;
+        sWo[o * LPAD + k] = (o < 2 * P) ? a.Wh[a.woff[4] + (int64_t)o * LW + k] : __float2half(0.f);
+    }
+    for (int i = tid; i < LW * 5; i += blockDim.x) sW1[i] = a.Wf[a.woff[0] + i];
+    for (int i = tid; i < 4 * LW; i += blockDim.x) sB[i] = a.Wf[a.boff[i / LW] + (i % LW)];
+    for (int i = tid; i < NOUT; i += blockDim.x) sB[4 * LW + i] = (i < 2 * P) ? a.Wf[a.boff[4] + i] : 0.f;
+    __syncthreads();
+
+    __half *myA = sAct + (warp * 2 + 0) * 16 * LPAD;
+    __half *myB = sAct + (warp * 2 + 1) * 16 * LPAD;
+    const int gid = lane >> 2, tig = lane & 3;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.nitems) break;
+        const int4 it = a.items[item];
+        const int bin = it.z;
+        const int S = a.bin_support[bin];
+        const int L = S * S;
+        const int plane = bin / (a.npa * a.nfb);
+        const int pab = (bin / a.nfb) % a.npa;
+        const bool rejected = a.plane_rejected && a.plane_rejected[plane];
+        const float chi_feat = (float)((a.pa_centres[pab] - a.chi_c) * a.inv_chi_h);
+        const int64_t tab0 = a.bin_offset ? a.bin_offset[bin] : 0;
+        for (int c0 = 0; c0 < it.y; c0 += LCHUNK) {
+            const int cnt = min(LCHUNK, it.y - c0);
+            __syncthreads();
+            // ---- stage: exact coordinates (FP64), flipped and weighted values
+            double wloc = 0.0;
+            unsigned long long nbad = 0;
+            for (int i = tid; i < cnt; i += blockDim.x) {
+                const aw_rec r = a.rec[it.x + c0 + i];
+                const uint32_t row = a.row[r.orig];
+                const uint16_t ch = a.chan[r.orig];
+                const double fq = a.freq[ch];
+                const double fl = fq / AW_C_LIGHT;
+                double u = a.uvw[3 * (int64_t)row] * fl, v = a.uvw[3 * (int64_t)row + 1] * fl;
+                double w = a.uvw[3 * (int64_t)row + 2] * fl;
+                if (w < 0) { u = -u; v = -v; w = -w; }
+                VisL e;
+                e.dx = (float)(u * a.cells_per_lambda + a.half_cells - (double)r.x0);
+                e.dy = (float)(v * a.cells_per_lambda + a.half_cells - (double)r.y0);
+                e.w = (float)w;
+                e.f = (float)fq;
+                e.pos = (int)r.x0 | ((int)r.y0 << 16);
+                e.koff = ((int)r.fy * a.OS + (int)r.fx) * L * P;
+                float2 vv[4] = {};
+                float ww[4] = {0, 0, 0, 0};
+                bool bad = false;
+                for (int c = 0; c < NPOL; ++c) {
+                    vv[c] = a.vis[(int64_t)r.orig * NPOL + c];
+                    ww[c] = a.weight ? a.weight[(int64_t)r.orig * NPOL + c] : 1.f;
+                    bad |= !isfinite(vv[c].x) || !isfinite(vv[c].y) || !isfinite(ww[c]);
+                }
+                if (r.flip) {
+                    for (int c = 0; c < NPOL; ++c) vv[c].y = -vv[c].y;
+                    if (NPOL == 4) {
+                        float2 t = vv[1]; vv[1] = vv[2]; vv[2] = t;
+                        float tw = ww[1]; ww[1] = ww[2]; ww[2] = tw;
+                    }
+                }
+                if (bad) {
+                    nbad++;
+                    for (int c = 0; c < NPOL; ++c) { vv[c] = make_float2(0.f, 0.f); ww[c] = 0.f; }
+                }
+                double wm = 0;
+                for (int c = 0; c < 4; ++c) {
+                    e.v[c] = (c < NPOL) ? make_float2(ww[c] * vv[c].x, ww[c] * vv[c].y) : make_float2(0.f, 0.f);
+                    if (c < NPOL) wm += ww[c];
+                }
+                wloc += wm / NPOL;
+                sv[i] = e;
+            }
+            for (int o = 16; o; o >>= 1) {
+                wloc += __shfl_xor_sync(0xffffffffu, wloc, o);
+                nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+            }
+            if (lane == 0) {
+                s_red[warp] = wloc;
+                if (nbad) atomicAdd(a.nonfinite, nbad);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0;
+                for (int w = 0; w < LWARPS; ++w) t += s_red[w];
+                atomicAdd(a.wsum, t);
+            }
+            // ---- points of this chunk, 16 rows per warp-tile
+            const int npts = cnt * L;
+            for (int t0 = warp * 16; t0 < npts; t0 += LWARPS * 16) {
+                // the two rows this lane owns in the fragment layout
+                int vi[2], gx[2], gy[2], tap[2];
+                bool ok[2];
+                for (int h = 0; h < 2; ++h) {
+                    const int p = t0 + gid + 8 * h;
+                    ok[h] = p < npts;
+                    const int pp = ok[h] ? p : 0;
+                    vi[h] = pp / L;
+                    tap[h] = pp - vi[h] * L;
+                    const int jy = tap[h] / S, jx = tap[h] - (tap[h] / S) * S;
+                    const int pos = sv[vi[h]].pos;
+                    gx[h] = (pos & 0xffff) + jx;
+                    gy[h] = (pos >> 16) + jy;
+                }
+                // K_{s, c = tig} for s = 0..NTO-1 (full pol) / K at tig == 0 (Stokes I), two rows
+                float kre[2][NTO], kim[2][NTO];
+                if (!rejected) {
+                    // layer 1 (5 -> 128) in FP32: lane pair per row, 64 outputs each
+                    {
+                        const int r = lane >> 1, half = lane & 1;
+                        const int p = t0 + r;
+                        float x[5] = {0, 0, 0, 0, 0};
+                        if (p < npts) {
+                            const int i = p / L, tp = p - (p / L) * L;
+                            const int jy = tp / S, jx = tp - (tp / S) * S;
+                            x[0] = ((float)jx - sv[i].dx) * a.inv_D;
+                            x[1] = ((float)jy - sv[i].dy) * a.inv_D;
+                            x[2] = sv[i].w * a.w_scale - 1.f;
+                            x[3] = (sv[i].f - a.f_c) * a.inv_f_h;
+                            x[4] = chi_feat;
+                        }
+                        for (int o = half * 64; o < half * 64 + 64; o += 2) {
+                            float z0 = sB[o], z1 = sB[o + 1];
+#pragma unroll
+                            for (int k = 0; k < 5; ++k) {
+                                z0 = fmaf(sW1[o * 5 + k], x[k], z0);
+                                z1 = fmaf(sW1[(o + 1) * 5 + k], x[k], z1);
+                            }
+                            *reinterpret_cast<__half2 *>(myA + r * LPAD + o) =
+                                __floats2half2_rn(__sinf(a.omega0 * z0), __sinf(a.omega0 * z1));
+                        }
+                    }
+                    __syncwarp();
+                    // layers 2..4 on tensor cores
+                    __half *src = myA, *dst = myB;
+                    for (int l = 0; l < 3; ++l) {
+                        float acc[LW / 8][4];
+                        warp_layer<LW / 8>(src, sW + l * LW * LPAD, sB + (l + 1) * LW, acc, lane);
+#pragma unroll
+                        for (int nt = 0; nt < LW / 8; ++nt) {
+                            const int col = nt * 8 + tig * 2;
+                            *reinterpret_cast<__half2 *>(dst + gid * LPAD + col) =
+                                __floats2half2_rn(__sinf(a.omega0 * acc[nt][0]), __sinf(a.omega0 * acc[nt][1]));
+                            *reinterpret_cast<__half2 *>(dst + (gid + 8) * LPAD + col) =
+                                __floats2half2_rn(__sinf(a.omega0 * acc[nt][2]), __sinf(a.omega0 * acc[nt][3]));
+                        }
+                        __syncwarp();
+                        __half *t = src; src = dst; dst = t;
+                    }
+                    // output layer
+                    float acc[NTO][4];
+                    warp_layer<NTO>(src, sWo, sB + 4 * LW, acc, lane);
+#pragma unroll
+                    for (int nt = 0; nt < NTO; ++nt) {
+                        kre[0][nt] = acc[nt][0] * a.out_scale;
+                        kim[0][nt] = acc[nt][1] * a.out_scale;
+                        kre[1][nt] = acc[nt][2] * a.out_scale;
+                        kim[1][nt] = acc[nt][3] * a.out_scale;
+                    }
+                } else {
+                    // fallback: the exact table values at the quantised offset
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int nt = 0; nt < NTO; ++nt) {
+                            kre[h][nt] = 0.f;
+                            kim[h][nt] = 0.f;
+                            const int m = (NPOL == 4) ? nt * 4 + tig : 0;
+                            if (ok[h] && (NPOL == 4 || tig == 0)) {
+                                const float2 k = read_tab(a.ktab, a.storage,
+                                                          tab0 + sv[vi[h]].koff + aw_tab_index(a.ce, L, tap[h], m));
+                                kre[h][nt] = k.x * a.inv_kscale;
+                                kim[h][nt] = k.y * a.inv_kscale;
+                            }
+                        }
+                }
+                // apply to the visibility and add to the grid
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 vq = sv[vi[h]].v[NPOL == 4 ? tig : 0];
+                    float2 cs[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const float kr = (s < NTO) ? kre[h][s] : 0.f, ki = (s < NTO) ? kim[h][s] : 0.f;
+                        cs[s] = make_float2(kr * vq.x - ki * vq.y, kr * vq.y + ki * vq.x);
+                    }
+                    if (NPOL == 4) {
+                        // sum over the correlation c = tig held by the 4 lanes of the quad
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            cs[s].x += __shfl_xor_sync(0xffffffffu, cs[s].x, 1);
+                            cs[s].y += __shfl_xor_sync(0xffffffffu, cs[s].y, 1);
+                            cs[s].x += __shfl_xor_sync(0xffffffffu, cs[s].x, 2);
+                            cs[s].y += __shfl_xor_sync(0xffffffffu, cs[s].y, 2);
+                        }
+                        if (ok[h])
+                            atomicAdd(a.grid + ((int64_t)tig * a.N + gy[h]) * a.N + gx[h], cs[tig]);
+                    } else if (ok[h] && tig == 0) {
+                        atomicAdd(a.grid + (int64_t)gy[h] * a.N + gx[h], cs[0]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t aw_learned_smem_bytes(int npol) {
+    const int P = npol * npol;
+    const int NOUT = (2 * P + 7) / 8 * 8;
+    return (size_t)(3 * LW * LPAD + NOUT * LPAD + LWARPS * 2 * 16 * LPAD) * sizeof(__half) +
+           (size_t)(LW * 5 + 4 * LW + NOUT) * sizeof(float) + (size_t)LCHUNK * sizeof(VisL);
+}
+
+int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,
+                           const double *d_pa, const void *vis, const float *weight, void *grid, int sm_count,
+                           cudaStream_t st) {
+    if (s->cfg.width != LW || s->cfg.n_hidden != 4)
+        return aw_set_error(AW_EUNSUPPORTED, "inline evaluation needs width 128 and 4 sine layers");
+    if (s->cfg.npol != p->npol) return aw_set_error(AW_EINVAL, "surrogate npol %d, plan npol %d", s->cfg.npol, p->npol);
+    if (p->nitems == 0) return AW_OK;
+    LearnArgs a;
+    a.rec = p->d_rec;
+    a.items = p->d_items;
+    a.nitems = p->nitems;
+    a.vis = reinterpret_cast<const float2 *>(vis);
+    a.weight = weight;
+    a.grid = reinterpret_cast<float2 *>(grid);
+    a.N = p->N;
+    a.OS = p->OS;
+    a.uvw = p->vis.uvw;
+    a.row = p->vis.row_of_vis;
+    a.chan = p->vis.chan_of_vis;
+    a.freq = p->vis.freq;
+    a.cells_per_lambda = p->uscale / p->OS;
+    a.half_cells = p->N / 2;
+    a.bin_support = fallback->d_bin_support;
+    a.npa = fallback->spec.npa;
+    a.nfb = fallback->spec.nfb;
+    a.pa_centres = d_pa;
+    a.Wh = s->d_ph;
+    a.Wf = s->d_p;
+    for (int l = 0; l < 5; ++l) {
+        a.woff[l] = s->woff[l];
+        a.boff[l] = s->boff[l];
+    }
+    a.omega0 = s->cfg.omega0;
+    a.inv_D = (float)(1.0 / s->cfg.D);
+    a.w_scale = (float)(s->cfg.w_max > 0 ? 2.0 / s->cfg.w_max : 0.0);
+    a.f_c = (float)s->cfg.f_c;
+    a.inv_f_h = (float)(1.0 / s->cfg.f_h);
+    a.chi_c = (float)s->cfg.chi_c;
+    a.inv_chi_h = (float)(1.0 / s->cfg.chi_h);
+    a.out_scale = s->cfg.out_scale;
+    a.plane_rejected = d_rejected;
+    a.ktab = fallback->d_table;
+    a.bin_offset = fallback->d_bin_offset;
+    a.storage = fallback->spec.storage;
+    a.ce = fallback->ce;
+    a.inv_kscale = 1.0f / fallback->scale;
+    a.wsum = p->d_wsum;
+    a.nonfinite = p->d_nonfinite;
+    a.counter = p->d_counter;
+    const size_t smem = aw_learned_smem_bytes(p->npol);
+    AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), st));
+    AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), st));
+    AW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st));
+    const int ctas = (int)std::min<int64_t>(p->nitems, sm_count);
+    if (p->npol == 4) {
+        AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        grid_learned_kernel<4><<<ctas, 256, smem, st>>>(a);
+    } else {
+        AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        grid_learned_kernel<1><<<ctas, 256, smem, st>>>(a);
+    }
+    AW_CHECK_LAUNCH();
+    return AW_OK;
+}

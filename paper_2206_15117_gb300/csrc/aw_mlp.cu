@@ -606,6 +606,8 @@ int aw_sur_init(aw_surrogate *s) {
 
 void aw_sur_free(aw_surrogate *s) {
     for (float *p : s->work) cudaFree(p);
+    if (s->d_rejected) cudaFree(s->d_rejected);
+    if (s->d_pa) cudaFree(s->d_pa);
     if (s->d_p) cudaFree(s->d_p);
     if (s->d_m) cudaFree(s->d_m);
     if (s->d_v) cudaFree(s->d_v);

@@ -21,7 +21,14 @@ struct aw_surrogate {
     std::vector<float *> Z, H;
     // per-w-plane rejection from the last aw_surrogate_tables call
     std::vector<uint8_t> plane_rejected;
+    // device copies used by the inline evaluation
+    uint8_t *d_rejected = nullptr;
+    double *d_pa = nullptr;
 };
+
+int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,
+                           const double *d_pa, const void *vis, const float *weight, void *grid, int sm_count,
+                           cudaStream_t st);
 
 int aw_sur_init(aw_surrogate *s);
 void aw_sur_free(aw_surrogate *s);

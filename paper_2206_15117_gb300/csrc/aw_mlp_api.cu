@@ -182,3 +182,38 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *s, const aw_kernel_set *exact
 }
 
 }  // extern "C"
+
+extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback,
+                               const void *vis, const float *weight, void *grid, aw_stats *stats, void *stream) {
+    SUR_GUARD_BEGIN
+    if (!ctx || !p || !s || !fallback || !grid || (!vis && p->nvis)) return aw_set_error(AW_EINVAL, "NULL argument");
+    if (p->N != fallback->spec.N || p->OS != fallback->spec.OS || p->nbins != fallback->nbins ||
+        p->bin_support != fallback->bin_support || p->npol != fallback->spec.npol)
+        return aw_set_error(AW_EINVAL, "fallback kernel set geometry does not match the plan");
+    int rc = set_dev(s->device);
+    if (rc) return rc;
+    cudaStream_t st = S_(stream);
+    const int nw = fallback->spec.nw, npa = fallback->spec.npa;
+    if (!s->d_rejected) AW_CUDA_TRY(cudaMalloc(&s->d_rejected, 256));
+    if (!s->d_pa) AW_CUDA_TRY(cudaMalloc(&s->d_pa, sizeof(double) * 256));
+    std::vector<uint8_t> rej(nw, 0);
+    for (int i = 0; i < nw && i < (int)s->plane_rejected.size(); ++i) rej[i] = s->plane_rejected[i];
+    AW_CUDA_TRY(cudaMemcpyAsync(s->d_rejected, rej.data(), nw, cudaMemcpyHostToDevice, st));
+    AW_CUDA_TRY(cudaMemcpyAsync(s->d_pa, fallback->pa.data(), sizeof(double) * npa, cudaMemcpyHostToDevice, st));
+    rc = aw_launch_grid_learned(p, s, fallback, s->d_rejected, s->d_pa, vis, weight, grid, ctx->sm_count, st);
+    if (rc) return rc;
+    if (stats) {
+        double ws = 0;
+        unsigned long long nb = 0;
+        AW_CUDA_TRY(cudaMemcpyAsync(&ws, p->d_wsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+        AW_CUDA_TRY(cudaMemcpyAsync(&nb, p->d_nonfinite, sizeof(nb), cudaMemcpyDeviceToHost, st));
+        AW_CUDA_TRY(cudaStreamSynchronize(st));
+        stats->n_nonfinite = (int64_t)nb;
+        stats->n_gridded = p->nvalid - (int64_t)nb;
+        stats->n_outside = p->n_outside;
+        stats->n_flagged = p->n_flagged;
+        stats->weight_sum = ws;
+    }
+    return AW_OK;
+    SUR_GUARD_END
+}

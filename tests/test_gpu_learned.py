@@ -1,0 +1,70 @@
+"""GPU: gridding with the surrogate evaluated inline (aw_grid_learned,
+tensor-core MLP inside the gridding kernel) against the FP64 oracle running
+the same network at the same continuous coordinates; and its exact-table
+fallback for rejected w planes against the oracle's exact gridding."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import core as oc
+from oracle import mlp as omlp
+from paper_2206_15117_gb300 import synthetic as sy
+from tests.gpu_cases import TOL_FP32, case_fullpol, oracle_coords, oracle_spec, rel_err, used_bins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2206_15117_gb300 import aw
+    return aw.aw_create(0)
+
+
+def _setup(ctx, n_t=10):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=n_t)
+    exact = aw.aw_make_kernels(ctx, **kw)
+    scales = dict(D=13.0, w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9, chi_c=0.0, chi_h=1.5, out_scale=0.02)
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, seed=5, **scales)
+    vd, keep = aw.device_observation(ob)
+    plan = aw.aw_plan_create(ctx, vd, exact)
+    vis = sy.random_vis(ob.nvis, 4, seed=31)
+    w = sy.random_weights(ob.nvis, 4, seed=32)
+    return ob, kw, exact, sur, plan, vis, w, scales, (vd, keep)
+
+
+def test_inline_surrogate_gridding_matches_oracle(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw, exact, sur, plan, vis, w, scales, keep = _setup(ctx)
+    grid = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
+    st = aw.aw_grid_learned(ctx, plan, sur, exact, torch.as_tensor(vis, device="cuda"),
+                            torch.as_tensor(w, device="cuda"), grid, want_stats=True)
+    g = grid.cpu().numpy()
+    spec = oracle_spec(kw)
+    co = oracle_coords(ob, kw)
+    p = aw.aw_surrogate_get_params(sur)
+    sizes = omlp.layer_sizes(5, 128, 4, 16)
+    sc = (scales["D"], scales["w_max"], scales["f_c"], scales["f_h"], scales["chi_c"], scales["chi_h"],
+          scales["out_scale"])
+    G = omlp.grid_inline(p, sizes, 30.0, sc, spec, ob.uvw, ob.row_of_vis, ob.chan_of_vis, ob.freq, co, vis, w)
+    l2, mx = rel_err(g, G)
+    # FP16 activations between the tensor-core layers: about 2^-11 relative per
+    # value, a few 1e-3 after four layers
+    assert l2 < 1e-2, (l2, mx)
+    assert np.abs(G).max() > 0
+    _, ws, _ = oc.grid(oc.make_kernels(spec, bins=used_bins(co)), co, vis, w)
+    assert st.weight_sum == pytest.approx(ws, rel=1e-12)
+
+
+def test_rejected_planes_fall_back_to_exact_tables(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw, exact, sur, plan, vis, w, scales, keep = _setup(ctx)
+    learned, err, nrej = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=0.0)   # reject every plane
+    assert nrej == aw.aw_kernel_set_info(exact).nbins
+    grid = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
+    aw.aw_grid_learned(ctx, plan, sur, exact, torch.as_tensor(vis, device="cuda"), torch.as_tensor(w, device="cuda"),
+                       grid)
+    co = oracle_coords(ob, kw)
+    G, _, _ = oc.grid(oc.make_kernels(oracle_spec(kw), bins=used_bins(co)), co, vis, w)
+    l2, mx = rel_err(grid.cpu().numpy(), G)
+    assert l2 < TOL_FP32 and mx < TOL_FP32, (l2, mx)
