@@ -54,6 +54,10 @@ def parse():
                     help="profiling case: only the visibilities of one (PA, frequency) bin pair, with its "
                          "32 w-plane kernels (same per-bin density and tables, 1/32 of the memory)")
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm (skips the autotuner)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
+    ap.add_argument("--learned-steps", type=int, default=8000)
+    ap.add_argument("--learned-fraction", type=float, default=0.1,
+                    help="fraction of the mosaic field's visibilities gridded by both kernel paths")
     return ap.parse_args()
 
 
@@ -223,6 +227,162 @@ def workload_config(ob, kw, info):
     return cfg
 
 
+# ----------------------------------------------------------------------------- learned surrogate
+def learned_section(ctx, dev, args):
+    """The learned AW-kernel surrogate on the mosaic workload: 4 x 128 SIREN
+    trained on the exact full-pol kernels of the configuration-2 bins (32 w
+    planes, supports 8-64, OS 8) x 8 PA x 4 frequency bins, then gridding one
+    mosaic field (2048^2, its own phase centre) with the network evaluated
+    inline and with the exact tables, on the same visibilities; plus the Eq. 1
+    weighting of the 7 hexagonal fields."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import synthetic as sy
+    stream = torch.cuda.current_stream()
+    ob = sy.observation(5, field=0)
+    g = sy.grid_geometry(5)
+    kw = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=7.0, npol=4, nw=32, w_max=ob.w_max,
+              supports=sy.w_supports(32), pa=list(ob.pa_centres), fbin_freqs=list(ob.fbin_freqs), dish_d=12.0,
+              d_xy=0.01 * np.exp(0.4j), d_yx=0.01 * np.exp(-1.3j), eps=0.2)
+    t0 = time.perf_counter()
+    exact = aw.aw_make_kernels(ctx, **kw)
+    t_synth = time.perf_counter() - t0
+    # 4x finer w sampling: the training set of the network and the reference
+    # the two gridding paths are judged against
+    kw_fine = {**kw, "nw": 128, "supports": sy.w_supports(128)}
+    fine = aw.aw_make_kernels(ctx, **kw_fine)
+    S0 = kw["supports"][0]
+    k0 = torch.empty(kw["OS"] ** 2 * S0 * S0 * 16, dtype=torch.complex64, device=dev)
+    aw.aw_kernel_set_export(exact, 0, k0)
+    kmax = float(k0.abs().max())
+    pa = np.asarray(kw["pa"])
+    chi_c = float(pa.mean())
+    chi_h = float(np.abs(pa - chi_c).max()) + 1e-3
+    # offsets normalised by the support of the 32-plane layout the network is used with
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, D=1.0,
+                                 norm_supports=kw["supports"], w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9,
+                                 chi_c=chi_c, chi_h=chi_h, out_scale=kmax, seed=17)
+    rep = aw.aw_surrogate_train(ctx, sur, fine, steps=args.learned_steps, batch=65536, lr=3e-4, lr_final=6e-6,
+                                seed=5)
+    reject = 0.05
+    t0 = time.perf_counter()
+    tabs, err, nrej = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=reject)
+    t_tables = time.perf_counter() - t0
+    del tabs
+    nw = kw["nw"]
+    per = len(kw["pa"]) * len(kw["fbin_freqs"])
+    plane_err = [float(err[p * per:(p + 1) * per].max()) for p in range(nw)]
+    # the same visibilities through both paths
+    rng = np.random.default_rng(11)
+    keep = np.sort(rng.choice(ob.nvis, size=max(1, int(ob.nvis * args.learned_fraction)), replace=False))
+    obs = sy.Observation(**{**ob.__dict__, "row_of_vis": ob.row_of_vis[keep], "chan_of_vis": ob.chan_of_vis[keep]})
+    vd, hold = aw.device_observation(obs, dev)
+    plan = aw.aw_plan_create(ctx, vd, exact, tune=aw.aw_tune(64, 128, 4, 0))
+    info = aw.aw_plan_query(plan)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(55)
+    vis = torch.randn((obs.nvis, 4), dtype=torch.complex64, device=dev, generator=gen)
+    N = kw["N"]
+    g_ex = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
+    g_le = torch.zeros_like(g_ex)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def run_exact():
+        g_ex.zero_()
+        aw.aw_grid_batched(ctx, plan, exact, vis, None, g_ex)
+
+    def run_learned():
+        g_le.zero_()
+        aw.aw_grid_learned(ctx, plan, sur, exact, vis, None, g_le)
+
+    img_ex = torch.empty((4, N, N), dtype=torch.float32, device=dev)
+    img_le = torch.empty_like(img_ex)
+    q = slice(N // 4, 3 * N // 4)
+
+    # reference: the exact kernels at 4x finer w sampling (128 planes)
+    plan_f = aw.aw_plan_create(ctx, vd, fine, tune=aw.aw_tune(64, 128, 4, 0))
+    info_f = aw.aw_plan_query(plan_f)
+    g_ref = torch.zeros_like(g_ex)
+    aw.aw_grid_batched(ctx, plan_f, fine, vis, None, g_ref)
+    img_ref = torch.empty_like(img_ex)
+    aw.aw_fft_to_image(ctx, fine, g_ref, float(info_f.nvalid), img_ref)
+    ref = img_ref[:, q, q]
+    ref_norm = torch.linalg.vector_norm(ref)
+
+    def err_vs_ref(g, kset):
+        img = torch.empty_like(img_ex)
+        aw.aw_fft_to_image(ctx, kset, g.clone(), float(info.nvalid), img)
+        d = (img - img_ref)[:, q, q]
+        return (float(torch.linalg.vector_norm(d) / ref_norm),
+                float(ref[0].abs().max() / (d[0].pow(2).mean().sqrt() + 1e-30)))
+
+    ms_ex = timed(run_exact)
+    ex_err, ex_dr = err_vs_ref(g_ex, exact)
+    # with the per-w-plane rejection of the tables call above
+    ms_le = timed(run_learned, reps=1)
+    img_err, dr = err_vs_ref(g_le, exact)
+    # the network inline on every plane (no rejection): its own speed and error
+    tabs2, _, _ = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=1e9)
+    del tabs2
+    ms_mlp = timed(run_learned, reps=1)
+    mlp_err, mlp_dr = err_vs_ref(g_le, exact)
+    points = float(info.mean_taps) * info.nvalid
+    mlp_flops = points * 2.0 * (5 * 128 + 3 * 128 * 128 + 128 * 32)
+    # generalisation between training samples: kernel error on an exact set
+    # sampled at OS 7 (offsets off the OS 8 training lattice) at the 32 plane
+    # centres (between the 128 training planes)
+    held = aw.aw_make_kernels(ctx, **{**kw, "OS": 7})
+    tabs3, err3, _ = aw.aw_surrogate_tables(ctx, sur, held, reject_rel=1e9)
+    del tabs3, held
+    plane_err_held = [float(err3[p * per:(p + 1) * per].max()) for p in range(nw)]
+    # Eq. 1 over the 7 hexagonal fields on a common 2048^2 frame (Airy power beams)
+    Nm = 2048
+    dlm = math.radians(4.0) / Nm
+    yy, xx = np.mgrid[0:Nm, 0:Nm]
+    beams = []
+    lam = 299792458.0 / 1.35e9
+    from scipy.special import j1
+    for (ex_deg, no_deg) in sy.mosaic_offsets():
+        r = np.hypot((xx - Nm // 2) * dlm - math.radians(ex_deg), (yy - Nm // 2) * dlm - math.radians(no_deg))
+        x = math.pi * 12.0 * r / lam
+        E = np.where(x == 0, 1.0, 2.0 * j1(np.where(x == 0, 1.0, x)) / np.where(x == 0, 1.0, x))
+        beams.append((E * E).astype(np.float32))
+    B = torch.as_tensor(np.stack(beams), device=dev)
+    gam = torch.empty((Nm, Nm), dtype=torch.float32, device=dev)
+    ms_gamma = timed(lambda: aw.mosaic_gamma(ctx, B, 0.2, gam), reps=10)
+    net_bytes = aw.aw_surrogate_nparams(sur) * 2
+    return {"workload": "mosaic field 0 of 7 (hexagonal, 1 deg), 2048^2 x 4, 1024 bins (32 w x 8 PA x 4 freq), "
+                        "supports 8-64, OS 8; %d of %d visibilities" % (obs.nvis, ob.nvis),
+            "mvis_s_learned_with_rejection": obs.nvis / (ms_le / 1e3) / 1e6,
+            "mvis_s_learned_inline_all_planes": obs.nvis / (ms_mlp / 1e3) / 1e6,
+            "mvis_s_exact_tables": obs.nvis / (ms_ex / 1e3) / 1e6,
+            "grid_ms_learned_with_rejection": ms_le, "grid_ms_learned_inline_all_planes": ms_mlp,
+            "grid_ms_exact": ms_ex,
+            "inline_mlp_points": points, "inline_mlp_tflops_fp16_mma": mlp_flops / (ms_mlp / 1e3) / 1e12,
+            "reference": "exact kernels at 128 w planes (4x finer); image errors over the inner half, Stokes I-V",
+            "dirty_image_rel_err_exact_32_planes_vs_ref": ex_err, "dynamic_range_exact_32_planes": ex_dr,
+            "dirty_image_rel_err_learned_with_rejection_vs_ref": img_err, "dynamic_range_learned_with_rejection": dr,
+            "dirty_image_rel_err_learned_all_planes_vs_ref": mlp_err, "dynamic_range_learned_all_planes": mlp_dr,
+            "train": {"steps": rep.steps, "batch": 65536, "seconds": rep.seconds, "loss_first": rep.loss_first,
+                      "loss_last": rep.loss_last, "set": "exact kernels at 128 w planes x 8 PA x 4 freq"},
+            "kernel_rel_l2_per_w_plane": [round(e, 4) for e in plane_err],
+            "kernel_rel_l2_per_w_plane_held_out_os7": [round(e, 4) for e in plane_err_held],
+            "reject_threshold": reject, "rejected_bins": int(nrej), "nbins": int(len(err)),
+            "network_bytes_fp16": int(net_bytes), "exact_table_bytes": int(aw.aw_kernel_set_info(exact).bytes),
+            "exact_synthesis_s": t_synth, "surrogate_tables_s": t_tables,
+            "mosaic_gamma_ms_7x2048^2": ms_gamma}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, dist):
     import torch
@@ -309,13 +469,9 @@ def run_ours(args, rank, world, dist):
     t_grid = [e[0].elapsed_time(e[1]) for e in evs]
     t_fft = [e[1].elapsed_time(e[2]) for e in evs]
     t_deg = [e[2].elapsed_time(e[3]) for e in evs]
-    if dist:
-        import torch.distributed as tdist
-        tt = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms, job_vis = aggregate(total_ms, nvis, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * nvis / (ms_per_step / 1e3) / 1e6
+    value = job_vis / (ms_per_step / 1e3) / 1e6
 
     # roofline of the dominant kernel: FP32 ALU (complex MACs of the Mueller product)
     flops = 128.0 * info.mean_taps * info.nvalid          # 16 complex MACs x 8 flop per tap
@@ -378,6 +534,12 @@ def run_ours(args, rank, world, dist):
                "d2h_bytes_per_step": int(nbytes), "ms_per_step": e_ms,
                "how": "pinned host visibilities copied in, grid + FFT + degrid, predicted visibilities copied out"}
 
+    learned = None
+    if not args.no_learned:
+        # free the FP32 workload before the learned comparison
+        del vis, vis_out, model, kd
+        torch.cuda.empty_cache()
+        learned = learned_section(ctx, dev, args)
     cpu = None
     if rank == 0 and not args.no_cpu:
         smp = oracle_sample(ob, kw, args.cpu_seconds)
@@ -398,9 +560,23 @@ def run_ours(args, rank, world, dist):
                 "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                            "reasons": clocks["reasons"]},
                 "gpu_launches": launches_per_step * args.steps,
-                "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm}}
+                "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm},
+                "learned": learned}
         print(json.dumps(line), flush=True)
     return 0
+
+
+def aggregate(total_ms: float, nvis: int, dist=None, device=None):
+    """Whole-job timing over replicas: the slowest rank's timed region (max)
+    and the visibilities of all ranks (sum)."""
+    if dist is None:
+        return float(total_ms), int(nvis)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(nvis)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
 
 
 def fp32_peak_tflops():

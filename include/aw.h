@@ -306,7 +306,10 @@ int aw_fft_to_image(aw_ctx *ctx, const aw_kernel_set *kset, void *grid, double w
  * (grid-minus-visibility offset d_u, d_v in cells, w in wavelengths,
  * frequency, parallactic angle) to the npol^2 complex Mueller kernel values
  * of that tap, and is trained on tables built by aw_make_kernels.
- *   features x = [d_u/D, d_v/D, 2 w/w_max - 1, (f - f_c)/f_h, (chi - chi_c)/chi_h]
+ *   features x = [d_u/s, d_v/s, 2 w/w_max - 1, (f - f_c)/f_h, (chi - chi_c)/chi_h],
+ *   s = D (S(w)/2 + 1), S(w) = norm_supports[min(floor(w norm_nw / w_max),
+ *   norm_nw - 1)]: offsets in units of the half support of the w plane that
+ *   |w| falls in, for one fixed plane layout shared by training and use
  *   layers [5, width x n_hidden, 2 npol^2]; hidden h = sin(omega0 (W h + b)),
  *   linear output; kernel value = output * out_scale.
  *   Parameters: one flat FP32 vector, per layer W [out][in] then b [out].
@@ -323,6 +326,8 @@ typedef struct aw_surrogate_cfg {
     double D, w_max, f_c, f_h, chi_c, chi_h;  /* feature scales (see above)      */
     float out_scale;         /* kernel value = output * out_scale                */
     uint64_t seed;           /* initialisation seed                              */
+    int32_t norm_nw;         /* planes of the offset-normalisation layout, 1..256 */
+    const int32_t *norm_supports;  /* host [norm_nw]: support per plane (copied) */
 } aw_surrogate_cfg;
 
 typedef struct aw_train_cfg {
@@ -374,7 +379,7 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exa
  * tables): for every visibility and tap of its footprint the MLP runs on
  * tensor cores (mma.sync, FP16 weights and activations, FP32 accumulation)
  * at the tap's exact offset from the visibility (no oversampling grid), the
- * visibility's exact |w| (no w-plane quantisation), its channel frequency
+ * visibility's exact |w| (no w-plane quantisation), its beam-frequency bin centre
  * and its parallactic-angle bin centre; the P kernel values are applied as
  * in aw_grid (same flip, weights, skip rules, accumulation into `grid`).
  * The plan gives the footprints (supports per w plane) and the order.  W

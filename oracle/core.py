@@ -578,3 +578,28 @@ def dft_adjoint(uvwl: np.ndarray, vis: np.ndarray, lm: np.ndarray) -> np.ndarray
 def pixel_lm(N: int, dl: float, qx: np.ndarray, qy: np.ndarray) -> np.ndarray:
     """(l, m) of image pixels (qy, qx): l = (qx - N/2) dl, m = (qy - N/2) dl."""
     return np.stack([(np.asarray(qx) - N // 2) * dl, (np.asarray(qy) - N // 2) * dl], axis=-1).astype(np.float64)
+
+
+def degrid_sampled(spec: KernelSpec, G: np.ndarray, co: Coords, idx) -> np.ndarray:
+    """Degridding of selected visibilities only, one by one, each with just the
+    kernel block of its own (bin, fine offset) synthesised (the same
+    definition as `degrid`, for grids too large to tabulate every bin).
+    Returns complex128 [len(idx)][npol]."""
+    npol = spec.npol
+    out = np.zeros((len(idx), npol), dtype=np.complex128)
+    for n, k in enumerate(idx):
+        if not co.valid[k]:
+            continue
+        b = int(co.bin[k])
+        S = int(spec.supports[b // (spec.npa * spec.nfb)])
+        K = synth_bin(spec, b, offsets_y=[int(co.fy[k])], offsets_x=[int(co.fx[k])])[0, 0]   # [S][S][P]
+        x0, y0 = int(co.x0[k]), int(co.y0[k])
+        win = np.asarray(G[:, y0:y0 + S, x0:x0 + S], dtype=np.complex128)                  # [s][S][S]
+        Km = K.reshape(S, S, npol, npol)                                                      # [jy][jx][c][s]
+        v = np.einsum("yxcs,syx->c", Km, win)
+        if co.flip[k]:
+            v = np.conj(v)
+            if npol == 4:
+                v = v[[0, 2, 1, 3]]
+        out[n] = v
+    return out

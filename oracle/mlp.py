@@ -6,9 +6,10 @@ per-bin FFT synthesis of Sec. 3.2 (the kernels it learns are the uv
 transforms of the Mueller cells times the anti-aliasing function and the w
 term).  Definitions shared with the CUDA path (written separately there):
 
-* features (5): x = [d_u / D, d_v / D, 2 w / w_max - 1, (f - f_c) / f_h,
+* features (5): x = [d_u / s, d_v / s, 2 w / w_max - 1, (f - f_c) / f_h,
   (chi - chi_c) / chi_h], with (d_u, d_v) the grid-minus-visibility offset of
-  the tap in cells;
+  the tap in cells and s = D (S(w)/2 + 1), S(w) = norm_supports[floor(w n /
+  w_max)] (clamped) for a fixed layout of n normalisation planes;
 * layers: sizes [5, H, H, H, H, 2P]; the first four apply
   h = sin(omega0 * (W h_prev + b)), the last is linear;
 * parameters: one flat vector, per layer W [out][in] row-major then b [out];
@@ -98,9 +99,13 @@ def adam_step(params, grads, m, v, t: int, lr: float, b1: float = 0.9, b2: float
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def features(du, dv, w, f, chi, D, w_max, f_c, f_h, chi_c, chi_h) -> np.ndarray:
+def features(du, dv, w, f, chi, D, norm_supports, w_max, f_c, f_h, chi_c, chi_h) -> np.ndarray:
     du = np.asarray(du, np.float64)
-    return np.stack([du / D, np.asarray(dv) / D, 2.0 * np.asarray(w) / w_max - 1.0,
+    w = np.asarray(w, np.float64)
+    ns = np.asarray(norm_supports)
+    pn = np.clip(np.floor(w * len(ns) / w_max).astype(np.int64), 0, len(ns) - 1)
+    s = D * (ns[pn] // 2 + 1)
+    return np.stack([du / s, np.asarray(dv) / s, 2.0 * w / w_max - 1.0,
                      (np.asarray(f) - f_c) / f_h, (np.asarray(chi) - chi_c) / chi_h], axis=-1)
 
 
@@ -111,15 +116,15 @@ def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vi
     For each gridded visibility (footprint x0, y0 and flip from the oracle's
     coordinate step) the tap (jy, jx) lies at d = (x0 + jx) - X cells from the
     visibility's exact position X = u N dl + N/2 (no oversampling grid); the
-    features use its exact |w|, its channel frequency and the centre of its
-    parallactic-angle bin; the network's 2P outputs times out_scale are the
+    features use its exact |w| and the centres of its beam-frequency and
+    parallactic-angle bins; the network's 2P outputs times out_scale are the
     Mueller kernel values K_{s,c}, and G[s][y][x] += sum_c K_{s,c} w'_c V'_c.
     With fp16_layers the weights of the tensor-core layers (all but the first)
     are rounded to FP16, as the GPU stores them.
-    `scales` = (D, w_max, f_c, f_h, chi_c, chi_h, out_scale).
+    `scales` = (D, norm_supports, w_max, f_c, f_h, chi_c, chi_h, out_scale).
     """
     from . import core as oc
-    D, w_max, f_c, f_h, chi_c, chi_h, out_scale = scales
+    D, norm_supports, w_max, f_c, f_h, chi_c, chi_h, out_scale = scales
     p = np.array(params, np.float64)
     if fp16_layers:
         layers = unpack(p, sizes)
@@ -154,8 +159,9 @@ def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vi
         du = (co.x0[k] + jx.ravel()) - X
         dv = (co.y0[k] + jy.ravel()) - Y
         nf = du.size
-        Xf = features(du, dv, np.full(nf, ww), np.full(nf, freq[chan_of_vis[k]]), np.full(nf, spec.pa[a]),
-                      D, w_max, f_c, f_h, chi_c, chi_h)
+        fb = b % spec.nfb
+        Xf = features(du, dv, np.full(nf, ww), np.full(nf, spec.fbin_freqs[fb]), np.full(nf, spec.pa[a]),
+                      D, norm_supports, w_max, f_c, f_h, chi_c, chi_h)
         out, _ = forward(p, sizes, Xf, omega0)
         K = (out[:, 0::2] + 1j * out[:, 1::2]) * out_scale          # [taps][P]
         K = K.reshape(S, S, npol, npol)                              # [jy][jx][s][c]

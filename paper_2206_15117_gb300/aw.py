@@ -95,7 +95,8 @@ SIGNATURES = {
 class aw_surrogate_cfg(ctypes.Structure):
     _fields_ = [("npol", c_i32), ("width", c_i32), ("n_hidden", c_i32), ("omega0", ctypes.c_float),
                 ("D", c_dbl), ("w_max", c_dbl), ("f_c", c_dbl), ("f_h", c_dbl), ("chi_c", c_dbl),
-                ("chi_h", c_dbl), ("out_scale", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("chi_h", c_dbl), ("out_scale", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("norm_nw", c_i32), ("norm_supports", ctypes.POINTER(c_i32))]
 
 
 class aw_train_cfg(ctypes.Structure):
@@ -363,10 +364,13 @@ def device_observation(ob, device="cuda:0", flags=None):
 
 # ---------------------------------------------------------------- learned surrogate
 def aw_surrogate_create(ctx: Handle, npol: int = 4, width: int = 128, n_hidden: int = 4, omega0: float = 30.0,
-                        D: float = 33.0, w_max: float = 1.0, f_c: float = 1.35e9, f_h: float = 0.15e9,
-                        chi_c: float = 0.0, chi_h: float = 1.5, out_scale: float = 0.02, seed: int = 1) -> Handle:
+                        D: float = 1.0, norm_supports=(8,), w_max: float = 1.0, f_c: float = 1.35e9,
+                        f_h: float = 0.15e9, chi_c: float = 0.0, chi_h: float = 1.5, out_scale: float = 0.02,
+                        seed: int = 1) -> Handle:
+    ns = (c_i32 * len(norm_supports))(*[int(x) for x in norm_supports])
     c = aw_surrogate_cfg(int(npol), int(width), int(n_hidden), float(omega0), float(D), float(w_max),
-                         float(f_c), float(f_h), float(chi_c), float(chi_h), float(out_scale), int(seed))
+                         float(f_c), float(f_h), float(chi_c), float(chi_h), float(out_scale), int(seed),
+                         len(norm_supports), ctypes.cast(ns, ctypes.POINTER(c_i32)))
     out = c_p()
     _check(load().aw_surrogate_create(ctx.ptr, ctypes.byref(c), ctypes.byref(out)), "aw_surrogate_create")
     h = Handle(out, "aw_surrogate_destroy")

@@ -387,7 +387,7 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
     cudaEventCreate(&e1);
     const int tiles[] = {16, 32, 64};
     const int chunks[] = {128, 256, 512};
-    const int ctas[] = {1, 2, 4};
+    const int ctas[] = {2, 4, 5};
     float best = 1e30f;
     aw_tune bt{32, 256, 2, 0};
     for (int t : tiles) {

@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) grid_items_kernel(GridArgs a) {
 
 // Persistent form: CTAs pull items from a device queue until it is empty.
 template <int NPOL, int ST>
-__global__ void __launch_bounds__(256) grid_persistent_kernel(GridArgs a) {
+__global__ void __launch_bounds__(256, 5) grid_persistent_kernel(GridArgs a) {
     extern __shared__ __align__(16) char smem[];
     __shared__ double red[8];
     __shared__ int next;

@@ -93,7 +93,7 @@ struct aw_plan {
     int N = 0, OS = 0, npol = 1, nbins = 0, nw = 1, npa = 1, nfb = 1;
     aw_tune tune{};
     double mean_taps = 0;
-    aw_rec *d_rec = nullptr;        // [nvis] sorted (valid first)
+    aw_rec *d_rec = nullptr;        // [nvis] sorted (valid first) by (bin, tile, position)
     int4 *d_items = nullptr;        // [nitems] {start, count, bin, tile}
     int32_t *d_plane_support = nullptr;  // [nw] support per w plane
     std::vector<int32_t> bin_support;

@@ -4,7 +4,7 @@
 // Mueller kernel values of that tap, which are applied to the visibility and
 // added to the grid.  The kernel coordinates are continuous: the exact
 // visibility position (no oversampling grid), its exact w (no w-plane
-// quantisation) and its channel frequency; no kernel table is read.  Items
+// quantisation) and the centre of its beam-frequency bin; no kernel table is read.  Items
 // whose w plane the surrogate was rejected on read the exact tables instead
 // (the same accumulation code, fed from memory).
 //
@@ -30,7 +30,8 @@ struct __align__(16) VisL {
     float w, f;      // |w| (wavelengths) and frequency (Hz)
     int pos;         // x0 | y0 << 16
     int koff;        // fallback table block offset (fy * OS + fx) * L * P
-    int pad0, pad1;
+    float inv_off;   // 1 / offset scale for this |w|
+    int pad1;
 };
 
 struct LearnArgs {
@@ -54,7 +55,10 @@ struct LearnArgs {
     const __half *Wh;
     const float *Wf;
     int64_t woff[5], boff[5];
-    float omega0, inv_D, w_scale, f_c, inv_f_h, chi_c, inv_chi_h, out_scale;
+    float omega0, w_scale, f_c, inv_f_h, chi_c, inv_chi_h, out_scale;
+    double D, w_max;          // offset scale D (S(w)/2 + 1), S from the normalisation planes
+    const int32_t *norm;
+    int norm_nw;
     const uint8_t *plane_rejected;
     // exact fallback tables
     const void *ktab;
@@ -191,7 +195,16 @@ __global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
                 e.dx = (float)(u * a.cells_per_lambda + a.half_cells - (double)r.x0);
                 e.dy = (float)(v * a.cells_per_lambda + a.half_cells - (double)r.y0);
                 e.w = (float)w;
-                e.f = (float)fq;
+                {
+                    int pn = a.w_max > 0 ? (int)floor(w * a.norm_nw / a.w_max) : 0;
+                    pn = min(max(pn, 0), a.norm_nw - 1);
+                    e.inv_off = (float)(1.0 / (a.D * (a.norm[pn] / 2 + 1)));
+                }
+                e.pad1 = 0;
+                // the beam frequency of the visibility's bin: the network was
+                // trained at the bin centres (the exact path averages the beam
+                // over the same channel range)
+                e.f = (float)a.pa_centres[a.npa + bin % a.nfb];
                 e.pos = (int)r.x0 | ((int)r.y0 << 16);
                 e.koff = ((int)r.fy * a.OS + (int)r.fx) * L * P;
                 float2 vv[4] = {};
@@ -263,8 +276,8 @@ __global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
                         if (p < npts) {
                             const int i = p / L, tp = p - (p / L) * L;
                             const int jy = tp / S, jx = tp - (tp / S) * S;
-                            x[0] = ((float)jx - sv[i].dx) * a.inv_D;
-                            x[1] = ((float)jy - sv[i].dy) * a.inv_D;
+                            x[0] = ((float)jx - sv[i].dx) * sv[i].inv_off;
+                            x[1] = ((float)jy - sv[i].dy) * sv[i].inv_off;
                             x[2] = sv[i].w * a.w_scale - 1.f;
                             x[3] = (sv[i].f - a.f_c) * a.inv_f_h;
                             x[4] = chi_feat;
@@ -396,7 +409,10 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
         a.boff[l] = s->boff[l];
     }
     a.omega0 = s->cfg.omega0;
-    a.inv_D = (float)(1.0 / s->cfg.D);
+    a.D = s->cfg.D;
+    a.norm = s->d_norm;
+    a.norm_nw = (int)s->norm.size();
+    a.w_max = s->cfg.w_max;
     a.w_scale = (float)(s->cfg.w_max > 0 ? 2.0 / s->cfg.w_max : 0.0);
     a.f_c = (float)s->cfg.f_c;
     a.inv_f_h = (float)(1.0 / s->cfg.f_h);

@@ -6,7 +6,8 @@
 // trained on the tables aw_make_kernels produces.
 //
 // Definitions (the FP64 oracle states the same ones independently):
-//   features x = [d_u/D, d_v/D, 2w/w_max - 1, (f - f_c)/f_h, (chi - chi_c)/chi_h]
+//   features x = [d_u/s, d_v/s, 2w/w_max - 1, (f - f_c)/f_h, (chi - chi_c)/chi_h],
+//   s = D (S(w)/2 + 1), S(w) the support of the normalisation plane of |w|
 //   layers [5, H x n_hidden, 2P]: h = sin(omega0 (W h + b)) for the hidden
 //   layers, linear output; flat parameters, per layer W [out][in] then b [out];
 //   loss L = (1/B) sum (y - t)^2 with t = kernel / out_scale; Adam with bias
@@ -172,6 +173,8 @@ struct SetView {
 
 struct FeatureScales {
     double D, w_max, f_c, f_h, chi_c, chi_h;
+    const int32_t *norm;   // [norm_nw] supports of the normalisation planes
+    int norm_nw;
     float out_scale;
 };
 
@@ -185,8 +188,12 @@ __device__ __forceinline__ void features_of(const SetView &v, const FeatureScale
     const double du = (double)(jx * v.OS - rho - fx) / v.OS;
     const double dv = (double)(jy * v.OS - rho - fy) / v.OS;
     const double w = v.nw > 1 ? (p + 0.5) * v.w_max / v.nw : 0.0;
-    x[0] = (float)(du / fs.D);
-    x[1] = (float)(dv / fs.D);
+    // offsets in units of the half support of the normalisation plane of |w|
+    int pn = fs.w_max > 0 ? (int)floor(w * fs.norm_nw / fs.w_max) : 0;
+    pn = min(max(pn, 0), fs.norm_nw - 1);
+    const double dsc = fs.D * (fs.norm[pn] / 2 + 1);
+    x[0] = (float)(du / dsc);
+    x[1] = (float)(dv / dsc);
     x[2] = (float)(fs.w_max > 0 ? 2.0 * w / fs.w_max - 1.0 : -1.0);
     x[3] = (float)((v.freq[f] - fs.f_c) / fs.f_h);
     x[4] = (float)((v.pa[a] - fs.chi_c) / fs.chi_h);
@@ -395,6 +402,8 @@ static SetView view_of(const aw_kernel_set *k, const double *d_pa, const double 
 static FeatureScales scales_of(const aw_surrogate *s) {
     FeatureScales f;
     f.D = s->cfg.D;
+    f.norm = s->d_norm;
+    f.norm_nw = (int)s->norm.size();
     f.w_max = s->cfg.w_max;
     f.f_c = s->cfg.f_c;
     f.f_h = s->cfg.f_h;
@@ -559,6 +568,11 @@ int aw_sur_sync_half(aw_surrogate *s, cudaStream_t st) {
 }
 
 int aw_sur_init(aw_surrogate *s) {
+    // the normalisation layout is owned by the surrogate from here on
+    s->norm.assign(s->cfg.norm_supports, s->cfg.norm_supports + s->cfg.norm_nw);
+    s->cfg.norm_supports = s->norm.data();
+    AW_CUDA_TRY(cudaMalloc(&s->d_norm, sizeof(int32_t) * s->norm.size()));
+    AW_CUDA_TRY(cudaMemcpy(s->d_norm, s->norm.data(), sizeof(int32_t) * s->norm.size(), cudaMemcpyHostToDevice));
     s->sizes.clear();
     s->sizes.push_back(5);
     for (int i = 0; i < s->cfg.n_hidden; ++i) s->sizes.push_back(s->cfg.width);
@@ -608,6 +622,7 @@ void aw_sur_free(aw_surrogate *s) {
     for (float *p : s->work) cudaFree(p);
     if (s->d_rejected) cudaFree(s->d_rejected);
     if (s->d_pa) cudaFree(s->d_pa);
+    if (s->d_norm) cudaFree(s->d_norm);
     if (s->d_p) cudaFree(s->d_p);
     if (s->d_m) cudaFree(s->d_m);
     if (s->d_v) cudaFree(s->d_v);

@@ -24,6 +24,9 @@ struct aw_surrogate {
     // device copies used by the inline evaluation
     uint8_t *d_rejected = nullptr;
     double *d_pa = nullptr;
+    // offset-normalisation plane layout (host copy and device copy)
+    std::vector<int32_t> norm;
+    int32_t *d_norm = nullptr;
 };
 
 int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,

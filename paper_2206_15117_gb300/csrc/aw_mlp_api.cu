@@ -36,6 +36,10 @@ int aw_surrogate_create(aw_ctx *ctx, const aw_surrogate_cfg *cfg, aw_surrogate *
         return aw_set_error(AW_EINVAL, "width %d / n_hidden %d out of range", cfg->width, cfg->n_hidden);
     if (!(cfg->D > 0) || !(cfg->f_h > 0) || !(cfg->chi_h > 0) || !(cfg->out_scale > 0))
         return aw_set_error(AW_EINVAL, "feature scales must be positive");
+    if (cfg->norm_nw < 1 || cfg->norm_nw > 256 || !cfg->norm_supports)
+        return aw_set_error(AW_EINVAL, "norm_nw %d / norm_supports", cfg->norm_nw);
+    for (int i = 0; i < cfg->norm_nw; ++i)
+        if (cfg->norm_supports[i] < 1) return aw_set_error(AW_EINVAL, "norm_supports[%d] < 1", i);
     int rc = set_dev(ctx->device);
     if (rc) return rc;
     aw_surrogate *s = new aw_surrogate();
@@ -199,7 +203,11 @@ extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, c
     std::vector<uint8_t> rej(nw, 0);
     for (int i = 0; i < nw && i < (int)s->plane_rejected.size(); ++i) rej[i] = s->plane_rejected[i];
     AW_CUDA_TRY(cudaMemcpyAsync(s->d_rejected, rej.data(), nw, cudaMemcpyHostToDevice, st));
+    // [npa parallactic-angle centres][nfb beam-frequency centres]
+    if (npa + fallback->spec.nfb > 256) return aw_set_error(AW_EUNSUPPORTED, "more than 256 PA + frequency bins");
     AW_CUDA_TRY(cudaMemcpyAsync(s->d_pa, fallback->pa.data(), sizeof(double) * npa, cudaMemcpyHostToDevice, st));
+    AW_CUDA_TRY(cudaMemcpyAsync(s->d_pa + npa, fallback->fbin_freqs.data(), sizeof(double) * fallback->spec.nfb,
+                                cudaMemcpyHostToDevice, st));
     rc = aw_launch_grid_learned(p, s, fallback, s->d_rejected, s->d_pa, vis, weight, grid, ctx->sm_count, st);
     if (rc) return rc;
     if (stats) {

@@ -104,7 +104,7 @@ __global__ void coords_kernel(CoordArgs a, uint64_t invalid_key, uint64_t *keys,
         rc.fx = (uint8_t)o.fx;
         rc.fy = (uint8_t)o.fy;
         rc.flip = (uint8_t)o.flip;
-        rc.pad0 = 0;
+        rc.pad0 = ok ? 1 : 0;   // gridded
         rc.pad1 = 0;
         recs[k] = rc;
     }
@@ -263,6 +263,7 @@ __global__ void emit_items_kernel(const uint32_t *starts, const uint32_t *itemba
         }
     }
 }
+
 
 __global__ void gather_rec_kernel(const aw_rec *in, const uint32_t *perm, int64_t n, aw_rec *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

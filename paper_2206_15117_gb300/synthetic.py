@@ -84,11 +84,23 @@ class Observation:
         return int(self.row_of_vis.shape[0])
 
 
-def _common_array(rng, n_t: int, ha_hours: float = 4.0):
+def mosaic_offsets(n_fields: int = 7, sep_deg: float = 1.0):
+    """Hexagonal pointing offsets (east, north) in degrees: the centre and six
+    neighbours at `sep_deg`."""
+    out = [(0.0, 0.0)]
+    for k in range(n_fields - 1):
+        a = k * math.pi / 3.0
+        out.append((sep_deg * math.cos(a), sep_deg * math.sin(a)))
+    return out
+
+
+def _common_array(rng, n_t: int, ha_hours: float = 4.0, offset_deg=(0.0, 0.0)):
     enu = antenna_enu(36, 1500.0, rng)
     lat = math.radians(LAT_DEG)
-    dec = math.radians(DEC_DEG)
-    ha = np.linspace(-ha_hours, ha_hours, n_t) * (math.pi / 12.0)
+    dec = math.radians(DEC_DEG + offset_deg[1])
+    # an eastward pointing offset shifts the hour angle by -offset / cos(dec)
+    dha = -math.radians(offset_deg[0]) / math.cos(math.radians(DEC_DEG))
+    ha = np.linspace(-ha_hours, ha_hours, n_t) * (math.pi / 12.0) + dha
     bxyz = baselines_xyz(enu, lat)
     uvw = earth_rotation_uvw(bxyz, ha, dec)
     pa_row = np.repeat(parallactic_angle(ha, lat, dec), bxyz.shape[0])
@@ -116,7 +128,7 @@ def _w_max(uvw: np.ndarray, freq: np.ndarray) -> float:
 
 
 def observation(cfg: int, *, time_samples: Optional[int] = None, vis_fraction: float = 1.0,
-                seed: Optional[int] = None) -> Observation:
+                seed: Optional[int] = None, field: int = 0) -> Observation:
     """Geometry of configuration `cfg` (1, 2, 3 or 5).
 
     cfg 1: 200 time samples, one channel at 1.4 GHz (126,000 visibilities).
@@ -124,7 +136,8 @@ def observation(cfg: int, *, time_samples: Optional[int] = None, vis_fraction: f
     cfg 3: 2000 time samples, 288 channels 1.200-1.487 GHz at 1 MHz, each
            channel keeps a random row subset of U[50k, 400k] rows (flagging);
            8 parallactic-angle bins, 4 beam-frequency bins.
-    cfg 5: per field, config 2's array/band with 993 samples x 16 channels.
+    cfg 5: per field, config 2's array/band with 993 samples x 16 channels
+           (10.0M visibilities), phase centre at the field's hexagonal offset.
     `vis_fraction` < 1 keeps a seeded random subset of the visibilities.
     """
     rng = np.random.default_rng(BASE_SEED + cfg if seed is None else seed)
@@ -139,7 +152,8 @@ def observation(cfg: int, *, time_samples: Optional[int] = None, vis_fraction: f
         npa, nfb = 1, 1
     elif cfg in (2, 5):
         n_t = time_samples or (2000 if cfg == 2 else 993)
-        uvw, pa_row = _common_array(rng, n_t)
+        off = mosaic_offsets()[field] if cfg == 5 else (0.0, 0.0)
+        uvw, pa_row = _common_array(rng, n_t, offset_deg=off)
         freq = np.linspace(1.2e9, 1.5e9, 16)
         nrow = uvw.shape[0]
         row = np.tile(np.arange(nrow, dtype=np.uint32), freq.size)

@@ -24,7 +24,8 @@ def _setup(ctx, n_t=10):
     from paper_2206_15117_gb300 import aw
     ob, kw = case_fullpol(n_t=n_t)
     exact = aw.aw_make_kernels(ctx, **kw)
-    scales = dict(D=13.0, w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9, chi_c=0.0, chi_h=1.5, out_scale=0.02)
+    scales = dict(D=1.0, norm_supports=list(kw["supports"]), w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9,
+                  chi_c=0.0, chi_h=1.5, out_scale=0.02)
     sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, seed=5, **scales)
     vd, keep = aw.device_observation(ob)
     plan = aw.aw_plan_create(ctx, vd, exact)
@@ -44,7 +45,8 @@ def test_inline_surrogate_gridding_matches_oracle(ctx):
     co = oracle_coords(ob, kw)
     p = aw.aw_surrogate_get_params(sur)
     sizes = omlp.layer_sizes(5, 128, 4, 16)
-    sc = (scales["D"], scales["w_max"], scales["f_c"], scales["f_h"], scales["chi_c"], scales["chi_h"],
+    sc = (scales["D"], scales["norm_supports"], scales["w_max"], scales["f_c"], scales["f_h"], scales["chi_c"],
+          scales["chi_h"],
           scales["out_scale"])
     G = omlp.grid_inline(p, sizes, 30.0, sc, spec, ob.uvw, ob.row_of_vis, ob.chan_of_vis, ob.freq, co, vis, w)
     l2, mx = rel_err(g, G)

@@ -72,7 +72,7 @@ def test_training_learns_the_kernels_and_rejects_per_plane(ctx):
     exact = aw.aw_make_kernels(ctx, **kw)
     ex = _export_all(aw, exact, kw)
     kmax = max(np.abs(e).max() for e in ex)
-    sur = aw.aw_surrogate_create(ctx, npol=1, width=64, n_hidden=4, omega0=30.0, D=9.0, w_max=kw["w_max"],
+    sur = aw.aw_surrogate_create(ctx, npol=1, width=64, n_hidden=4, omega0=30.0, D=1.0, norm_supports=kw["supports"], w_max=kw["w_max"],
                                  f_c=1.4e9, f_h=0.2e9, chi_c=0.0, chi_h=1.5, out_scale=float(kmax), seed=11)
     rep = aw.aw_surrogate_train(ctx, sur, exact, steps=600, batch=8192, lr=1e-3, lr_final=1e-5, seed=3)
     assert rep.steps == 600 and rep.loss_last < 0.05 * rep.loss_first, (rep.loss_first, rep.loss_last)
