@@ -283,7 +283,7 @@ struct DegridArgs {
 };
 
 template <int NPOL, int ST>
-__global__ void __launch_bounds__(256) degrid_warp_kernel(DegridArgs a) {
+__global__ void __launch_bounds__(256, 5) degrid_warp_kernel(DegridArgs a) {
     constexpr int P = NPOL * NPOL;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
