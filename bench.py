@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--subset", action="store_true",
                     help="profiling case: only the visibilities of one (PA, frequency) bin pair, with its "
                          "32 w-plane kernels (same per-bin density and tables, 1/32 of the memory)")
-    ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm (skips the autotuner)")
+    ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
     ap.add_argument("--learned-steps", type=int, default=8000)
     ap.add_argument("--learned-fraction", type=float, default=0.1,
@@ -415,7 +415,8 @@ def run_ours(args, rank, world, dist):
     vd_sub, keep_sub = aw.device_observation(ob_sub, dev)
     t0 = time.perf_counter()
     if args.tune:
-        tune = aw.aw_tune(*[int(x) for x in args.tune.split(",")], 0)
+        tv = [int(x) for x in args.tune.split(",")]
+        tune = aw.aw_tune(*(tv + [0] * (5 - len(tv))))
     else:
         tune = aw.aw_autotune(ctx, vd_sub, kg)
     t_tune = time.perf_counter() - t0
@@ -560,7 +561,9 @@ def run_ours(args, rank, world, dist):
                 "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                            "reasons": clocks["reasons"]},
                 "gpu_launches": launches_per_step * args.steps,
-                "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm},
+                "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm,
+                         "dg_tile": tune.dg_tile or 256, "degrid_items": info.nitems_degrid,
+                         "grid_schedule": ["tiles", "offsets"][tune.grid_mode]},
                 "learned": learned}
         print(json.dumps(line), flush=True)
     return 0

@@ -120,8 +120,20 @@ typedef struct aw_tune {
     int32_t tile;            /* grid tile side for the visibility sort, 8..256 (power of 2) */
     int32_t chunk;           /* max visibilities per work item, 32..2048          */
     int32_t ctas_per_sm;     /* persistent launch: CTAs per SM, 1..8              */
-    int32_t reserved;
+    int32_t dg_tile;         /* degridding super-tile side (power of 2, 32..4096);
+                              * 0 selects 256.  Degridding visits visibilities
+                              * grouped by (bin, super-tile, oversampled offset) */
+    int32_t grid_mode;       /* AW_GRID_TILES or AW_GRID_OFFSETS (below)           */
 } aw_tune;
+
+/* Gridding schedules (aw_tune.grid_mode).  TILES: work items of one bin and
+ * one grid tile, register accumulation per residue class of the support,
+ * persistent launch (tile, chunk, ctas_per_sm apply).  OFFSETS: the
+ * degridding items (one bin, super-tile and oversampled offset), each kernel
+ * tap loaded once per item and added for every visibility with vector
+ * atomics (dg_tile applies).  Both give the same grid up to FP32 rounding
+ * order. */
+enum { AW_GRID_TILES = 0, AW_GRID_OFFSETS = 1 };
 
 typedef struct aw_plan_info {
     int64_t nvis;
@@ -132,6 +144,7 @@ typedef struct aw_plan_info {
     int32_t tile;
     int32_t chunk;
     double mean_taps;        /* mean S^2 over the valid visibilities              */
+    int64_t nitems_degrid;   /* degridding work items                             */
 } aw_plan_info;
 
 typedef struct aw_stats {
@@ -264,10 +277,10 @@ int aw_degrid(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const
               void *vis_out, void *stream);
 
 /*
- * aw_grid_batched - aw_grid as one persistent launch over the plan's work
- * queue (every channel, polarisation and w plane of uneven counts in one
- * launch), captured once in a CUDA graph and replayed.  ctas_per_sm from the
- * plan's tune.  The graph is cached in the plan for the last (vis, weight,
+ * aw_grid_batched - aw_grid as one launch over all the plan's work items
+ * (every channel, polarisation and w plane of uneven counts in one launch),
+ * captured once in a CUDA graph and replayed.  With grid_mode TILES the
+ * launch is persistent over a work queue, ctas_per_sm from the plan's tune.  The graph is cached in the plan for the last (vis, weight,
  * grid, kset) pointers; do not call it for one plan from two threads.
  * Same result as aw_grid within FP32 summation-order rounding.
  */
@@ -276,8 +289,9 @@ int aw_grid_batched(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kset, const
 
 /*
  * aw_autotune - time aw_grid_batched over candidate (tile, chunk,
- * ctas_per_sm) on the given visibilities (pass a subsample to keep it short)
- * and return the fastest in *out.  Uses a scratch grid it allocates.
+ * ctas_per_sm) of the TILES schedule and two super-tile sizes of the OFFSETS
+ * schedule on the given visibilities (pass a subsample to keep it short) and
+ * return the fastest in *out.  Uses a scratch grid it allocates.
  * Synchronises `stream`.
  */
 int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset, aw_tune *out,

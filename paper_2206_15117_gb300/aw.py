@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libaw.so")
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ETIMEOUT, AW_EUNSUPPORTED, AW_EREJECTED = range(7)
 AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT = 0, 1, 2
 AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
+AW_GRID_TILES, AW_GRID_OFFSETS = 0, 1
 
 c_i32, c_i64, c_dbl, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -43,12 +44,14 @@ class aw_vis_desc(ctypes.Structure):
 
 
 class aw_tune(ctypes.Structure):
-    _fields_ = [("tile", c_i32), ("chunk", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32)]
+    _fields_ = [("tile", c_i32), ("chunk", c_i32), ("ctas_per_sm", c_i32), ("dg_tile", c_i32),
+                ("grid_mode", c_i32)]
 
 
 class aw_plan_info(ctypes.Structure):
     _fields_ = [("nvis", c_i64), ("nvalid", c_i64), ("n_outside", c_i64), ("n_flagged", c_i64),
-                ("nitems", c_i64), ("tile", c_i32), ("chunk", c_i32), ("mean_taps", c_dbl)]
+                ("nitems", c_i64), ("tile", c_i32), ("chunk", c_i32), ("mean_taps", c_dbl),
+                ("nitems_degrid", c_i64)]
 
 
 class aw_stats(ctypes.Structure):

@@ -200,6 +200,8 @@ static void free_plan(aw_plan *p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->d_rec) cudaFree(p->d_rec);
     if (p->d_items) cudaFree(p->d_items);
+    if (p->d_rec_dg) cudaFree(p->d_rec_dg);
+    if (p->d_items_dg) cudaFree(p->d_items_dg);
     if (p->d_plane_support) cudaFree(p->d_plane_support);
     if (p->d_wsum) cudaFree(p->d_wsum);
     if (p->d_nonfinite) cudaFree(p->d_nonfinite);
@@ -233,6 +235,7 @@ int aw_plan_query(const aw_plan *p, aw_plan_info *info) {
     info->tile = p->tune.tile;
     info->chunk = p->tune.chunk;
     info->mean_taps = p->mean_taps;
+    info->nitems_degrid = p->nitems_dg;
     return AW_OK;
 }
 
@@ -389,35 +392,58 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
     const int chunks[] = {128, 256, 512};
     const int ctas[] = {2, 4, 5};
     float best = 1e30f;
-    aw_tune bt{32, 256, 2, 0};
+    aw_tune bt{32, 256, 2, 0, AW_GRID_TILES};
+    // one timing of aw_grid_batched on plan p: best of reps 2..3
+    auto time_plan = [&](aw_plan *p, float *ms_out) -> int {
+        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        float ms_best = 1e30f;
+        int r = AW_OK;
+        for (int rep = 0; rep < 3 && r == AW_OK; ++rep) {
+            cudaMemsetAsync(grid, 0, gbytes, s);
+            cudaEventRecord(e0, s);
+            r = aw_grid_batched(ctx, p, k, v, nullptr, grid, nullptr, stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < ms_best) ms_best = ms;
+        }
+        *ms_out = ms_best;
+        return r;
+    };
     for (int t : tiles) {
         for (int c : chunks) {
-            aw_tune tu{t, c, 1, 0};
+            aw_tune tu{t, c, 1, 0, AW_GRID_TILES};
             aw_plan *p = new aw_plan();
             p->device = ctx->device;
             rc = aw_plan_build(ctx, vis, k, &tu, p, s);
             if (rc) { free_plan(p); break; }
             for (int cp : ctas) {
                 p->tune.ctas_per_sm = cp;
-                if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
                 float ms_best = 1e30f;
-                for (int rep = 0; rep < 3 && rc == AW_OK; ++rep) {
-                    cudaMemsetAsync(grid, 0, gbytes, s);
-                    cudaEventRecord(e0, s);
-                    rc = aw_grid_batched(ctx, p, k, v, nullptr, grid, nullptr, stream);
-                    cudaEventRecord(e1, s);
-                    cudaEventSynchronize(e1);
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0 && ms < ms_best) ms_best = ms;
-                }
+                rc = time_plan(p, &ms_best);
                 if (rc) break;
-                if (ms_best < best) { best = ms_best; bt = aw_tune{t, c, cp, 0}; }
+                if (ms_best < best) { best = ms_best; bt = aw_tune{t, c, cp, 0, AW_GRID_TILES}; }
             }
             free_plan(p);
             if (rc) break;
         }
         if (rc) break;
+    }
+    // the offset-grouped schedule, over two super-tile sizes
+    const int dg_tiles[] = {256, 1024};
+    for (int dt : dg_tiles) {
+        if (rc) break;
+        aw_tune tu{bt.tile, bt.chunk, bt.ctas_per_sm, dt, AW_GRID_OFFSETS};
+        aw_plan *p = new aw_plan();
+        p->device = ctx->device;
+        rc = aw_plan_build(ctx, vis, k, &tu, p, s);
+        if (rc) { free_plan(p); break; }
+        float ms_best = 1e30f;
+        rc = time_plan(p, &ms_best);
+        free_plan(p);
+        if (rc) break;
+        if (ms_best < best) { best = ms_best; bt = tu; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

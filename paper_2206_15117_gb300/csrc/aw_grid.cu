@@ -16,9 +16,10 @@
 // atomic per plane when the cell changes.  The 4x4 Mueller kernel of a tap
 // (16 complex values, 128 B in FP32) is read with 128-bit loads.
 //
-// Degridding: one warp per visibility; lanes stride over the S x S taps,
-// each tap a (npol x npol) complex kernel times npol grid values, then a
-// warp-shuffle reduction.
+// Degridding: visibilities grouped by (bin, grid super-tile, oversampled
+// offset) share one kernel block; a CTA stages that block in shared memory
+// and applies it to up to 32 visibilities, each tap an (npol x npol) complex
+// kernel times npol grid values read from the super-tile (L2-resident).
 #include <algorithm>
 
 #include "aw_internal.h"
@@ -270,8 +271,141 @@ __global__ void __launch_bounds__(256, 5) grid_persistent_kernel(GridArgs a) {
     }
 }
 
+// Offset-grouped form of gridding, over the degridding items (visibilities
+// that share the bin and the oversampled offset, hence one kernel block).
+// A task is one tap t of the block and one residue class p of the item's
+// visibilities modulo nsplit: it loads the P Mueller values of tap t once and
+// applies them to every visibility of its class, adding each product to the
+// grid with one vector atomic per plane.  nsplit makes the task count a
+// multiple of the CTA size.  Weight-sum and non-finite statistics are kept
+// per thread over all its items and reduced once at the end.
+struct GridOffArgs {
+    const aw_rec *rec_dg;
+    const int4 *items;
+    int64_t nitems;
+    const void *ktab;
+    const int64_t *bin_offset;
+    const int32_t *bin_support;
+    const float2 *vis;
+    const float *weight;
+    float2 *grid;
+    int N, OS;
+    double *wsum;
+    unsigned long long *nonfinite;
+    float inv_scale;
+};
+
+__host__ __device__ inline int gcd_i(int a, int b) {
+    while (b) { const int t = a % b; a = b; b = t; }
+    return a;
+}
+
+template <int NPOL, int ST>
+__global__ void __launch_bounds__(256) grid_offset_kernel(GridOffArgs a) {
+    constexpr int P = NPOL * NPOL;
+    __shared__ __align__(16) float2 s_v[AW_DG_CHUNK * NPOL];
+    __shared__ int2 s_pos[AW_DG_CHUNK];
+    __shared__ double red[8];
+    __shared__ unsigned long long redn[8];
+    const int64_t plane = (int64_t)a.N * a.N;
+    double wloc = 0.0;
+    unsigned long long nbad = 0;
+    for (int64_t item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        const int4 it = a.items[item];
+        const int start = it.x, count = it.y, bin = it.z;
+        const int S = a.bin_support[bin];
+        const int L = S * S;
+        const float invS = 1.0f / (float)S;
+        __syncthreads();  // the previous item has finished with s_v / s_pos
+        if ((int)threadIdx.x < count) {
+            const aw_rec r = a.rec_dg[start + threadIdx.x];
+            float2 v[NPOL];
+            float w[NPOL];
+            bool bad = false;
+#pragma unroll
+            for (int c = 0; c < NPOL; ++c) {
+                v[c] = a.vis[(int64_t)r.orig * NPOL + c];
+                w[c] = a.weight ? a.weight[(int64_t)r.orig * NPOL + c] : 1.0f;
+                bad |= !isfinite(v[c].x) || !isfinite(v[c].y) || !isfinite(w[c]);
+            }
+            if (r.flip) {
+#pragma unroll
+                for (int c = 0; c < NPOL; ++c) v[c].y = -v[c].y;
+                if (NPOL == 4) {
+                    float2 t = v[1]; v[1] = v[2]; v[2] = t;
+                    float tw = w[1]; w[1] = w[2]; w[2] = tw;
+                }
+            }
+            if (bad) {
+                nbad++;
+#pragma unroll
+                for (int c = 0; c < NPOL; ++c) { v[c] = make_float2(0.f, 0.f); w[c] = 0.f; }
+            }
+            double wm = 0.0;
+#pragma unroll
+            for (int c = 0; c < NPOL; ++c) {
+                wm += (double)w[c];
+                const float ws = w[c] * a.inv_scale;
+                s_v[threadIdx.x * NPOL + c] = make_float2(ws * v[c].x, ws * v[c].y);
+            }
+            wloc += wm / NPOL;
+            s_pos[threadIdx.x] = make_int2(r.x0, r.y0);
+        }
+        __syncthreads();
+        const aw_rec r0 = a.rec_dg[start];
+        const int64_t kbase = a.bin_offset[bin] + (int64_t)(r0.fy * a.OS + r0.fx) * L * P;
+        const int nsplit = min(256 / gcd_i(L, 256), 8);
+        const int ntask = L * nsplit;
+        for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+            const int p = task / L, t = task - p * L;  // lanes on consecutive taps
+            const int jy = (int)(((float)t + 0.5f) * invS);
+            const int jx = t - jy * S;
+            float2 k[P];
+            load_k<ST, P>(a.ktab, kbase, L, t, k);
+            for (int j = p; j < count; j += nsplit) {
+                float2 v[NPOL];
+                if constexpr (NPOL == 4) {
+                    const float4 v01 = reinterpret_cast<const float4 *>(s_v)[2 * j];
+                    const float4 v23 = reinterpret_cast<const float4 *>(s_v)[2 * j + 1];
+                    v[0] = make_float2(v01.x, v01.y); v[1] = make_float2(v01.z, v01.w);
+                    v[2] = make_float2(v23.x, v23.y); v[3] = make_float2(v23.z, v23.w);
+                } else {
+                    v[0] = s_v[j];
+                }
+                const int2 pos = s_pos[j];
+                float2 *dst = a.grid + (int64_t)(pos.y + jy) * a.N + (pos.x + jx);
+#pragma unroll
+                for (int s = 0; s < NPOL; ++s) {
+                    float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c) cmac(o, k[s * NPOL + c], v[c]);
+                    atomicAdd(dst + s * plane, o);
+                }
+            }
+        }
+    }
+    // statistics: one atomic per CTA
+    for (int o = 16; o; o >>= 1) {
+        wloc += __shfl_xor_sync(0xffffffffu, wloc, o);
+        nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[warp] = wloc; redn[warp] = nbad; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tw = 0.0;
+        unsigned long long tn = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tw += red[w]; tn += redn[w]; }
+        atomicAdd(a.wsum, tw);
+        if (tn) atomicAdd(a.nonfinite, tn);
+    }
+}
+
 struct DegridArgs {
-    const aw_rec *rec;
+    const aw_rec *rec;       // grid order: [nvalid, nvis) are the visibilities not gridded
+    const aw_rec *rec_dg;    // [nvalid] degridding order
+    const int4 *items;       // [nitems] {start, count, bin, 0} over rec_dg
+    int64_t nitems;
     int64_t nvis, nvalid;
     const void *ktab;
     const int64_t *bin_offset;
@@ -282,50 +416,145 @@ struct DegridArgs {
     float inv_scale;
 };
 
+constexpr int DG_TS = 256;  // taps per shared-memory slab of the kernel block
+
+// Warp sum of x[0..2H) over the 32 lanes, halving the values held at each
+// step (reduce-scatter): for 2H == 32, lane l returns with the sum of x[l] in x[0].
+template <int H>
+__device__ __forceinline__ void reduce_scatter_step(float *x, int lane) {
+    const bool up = (lane & H) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float send = up ? x[i] : x[i + H];
+        const float keep = up ? x[i + H] : x[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, H);
+    }
+    if constexpr (H > 1) reduce_scatter_step<H / 2>(x, lane);
+}
+
+// One CTA per work item: up to AW_DG_CHUNK visibilities that share the bin
+// and the oversampled offset (fy, fx), hence one kernel block of S*S taps.
+// The block is staged in shared memory in slabs of DG_TS taps (converted to
+// FP32) and applied to every visibility of the item, so the kernel table is
+// read once per item instead of once per visibility.  The visibilities are
+// dealt to ngp warp groups (v = g + ngp * j, j < AW_DG_VB); the warps of a
+// group split the taps; lanes stride over taps and hold AW_DG_VB x NPOL
+// complex partial sums, reduced over the warp and then across the group's
+// warps in shared memory.
 template <int NPOL, int ST>
-__global__ void __launch_bounds__(256, 5) degrid_warp_kernel(DegridArgs a) {
+__global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
     constexpr int P = NPOL * NPOL;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < a.nvis; i += warps) {
-        const aw_rec r = a.rec[i];
-        if (i >= a.nvalid) {
-            if (lane < NPOL) a.vis_out[(int64_t)r.orig * NPOL + lane] = make_float2(0.f, 0.f);
-            continue;
-        }
-        const int S = a.bin_support[r.bin];
+    constexpr int VB = AW_DG_VB;
+    constexpr int NV = VB * NPOL * 2;  // partial sums per lane
+    __shared__ __align__(16) float2 s_k[DG_TS * P];
+    __shared__ float s_out[AW_DG_CHUNK * NPOL * 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t plane = (int64_t)a.N * a.N;
+    for (int64_t item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        const int4 it = a.items[item];
+        const int start = it.x, count = it.y, bin = it.z;
+        const int S = a.bin_support[bin];
         const int L = S * S;
-        const int64_t kbase = a.bin_offset[r.bin] + (int64_t)(r.fy * a.OS + r.fx) * L * P;  // block start
-        const float2 *g0 = a.grid + (int64_t)r.y0 * a.N + r.x0;
-        const int64_t plane = (int64_t)a.N * a.N;
-        float2 acc[NPOL];
+        const float invS = 1.0f / (float)S;
+        const aw_rec r0 = a.rec_dg[start];
+        const int64_t kbase = a.bin_offset[bin] + (int64_t)(r0.fy * a.OS + r0.fx) * L * P;
+        const int need = (count + VB - 1) / VB;
+        const int ngp = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
+        const int wpg = 8 / ngp;
+        const int g = warp & (ngp - 1), ph = warp / ngp;
+        const float2 *gb[VB];
+        bool has[VB];
 #pragma unroll
-        for (int c = 0; c < NPOL; ++c) acc[c] = make_float2(0.f, 0.f);
-        int jy = lane / S, jx = lane - jy * S;
-        for (int t = lane; t < L; t += 32) {
-            float2 k[P];
-            load_k<ST, P>(a.ktab, kbase, L, t, k);
-            const float2 *gp = g0 + (int64_t)jy * a.N + jx;
-            float2 gv[NPOL];
-#pragma unroll
-            for (int s = 0; s < NPOL; ++s) gv[s] = __ldg(gp + s * plane);
-#pragma unroll
-            for (int c = 0; c < NPOL; ++c)
-#pragma unroll
-                for (int s = 0; s < NPOL; ++s) cmac(acc[c], k[c * NPOL + s], gv[s]);
-            jx += 32;
-            while (jx >= S) { jx -= S; ++jy; }
+        for (int j = 0; j < VB; ++j) {
+            const int v = g + ngp * j;
+            has[j] = v < count;
+            const aw_rec r = has[j] ? a.rec_dg[start + v] : r0;
+            gb[j] = a.grid + (int64_t)r.y0 * a.N + r.x0;
         }
+        float acc[NV];
 #pragma unroll
-        for (int c = 0; c < NPOL; ++c)
-            for (int o = 16; o; o >>= 1) {
-                acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
-                acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+        for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+        __syncthreads();  // the previous item has finished with s_out and s_k
+        for (int i = threadIdx.x; i < count * NPOL * 2; i += blockDim.x) s_out[i] = 0.f;
+        for (int t0 = 0; t0 < L; t0 += DG_TS) {
+            const int ns = min(DG_TS, L - t0);
+            __syncthreads();
+            for (int tl = threadIdx.x; tl < ns; tl += blockDim.x) {
+                float2 k[P];
+                load_k<ST, P>(a.ktab, kbase, L, t0 + tl, k);
+                if constexpr (P % 2 == 0) {
+#pragma unroll
+                    for (int c = 0; c < P / 2; ++c)
+                        reinterpret_cast<float4 *>(s_k)[c * DG_TS + tl] =
+                            make_float4(k[2 * c].x, k[2 * c].y, k[2 * c + 1].x, k[2 * c + 1].y);
+                } else {
+                    s_k[tl] = k[0];
+                }
             }
-        if (lane == 0) {
+            __syncthreads();
+            for (int tl = ph * 32 + lane; tl < ns; tl += wpg * 32) {
+                const int t = t0 + tl;
+                const int jy = (int)(((float)t + 0.5f) * invS);
+                const int toff = jy * a.N + (t - jy * S);
+                float2 k[P];
+                if constexpr (P % 2 == 0) {
+#pragma unroll
+                    for (int c = 0; c < P / 2; ++c) {
+                        const float4 q = reinterpret_cast<const float4 *>(s_k)[c * DG_TS + tl];
+                        k[2 * c] = make_float2(q.x, q.y);
+                        k[2 * c + 1] = make_float2(q.z, q.w);
+                    }
+                } else {
+                    k[0] = s_k[tl];
+                }
+#pragma unroll
+                for (int j = 0; j < VB; ++j) {
+                    if (!has[j]) continue;
+                    float2 gv[NPOL];
+#pragma unroll
+                    for (int s = 0; s < NPOL; ++s) gv[s] = __ldg(gb[j] + toff + s * plane);
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c) {
+                        float re = acc[(j * NPOL + c) * 2], im = acc[(j * NPOL + c) * 2 + 1];
+#pragma unroll
+                        for (int s = 0; s < NPOL; ++s) {
+                            const float2 kk = k[c * NPOL + s];
+                            re = fmaf(kk.x, gv[s].x, re);
+                            re = fmaf(-kk.y, gv[s].y, re);
+                            im = fmaf(kk.x, gv[s].y, im);
+                            im = fmaf(kk.y, gv[s].x, im);
+                        }
+                        acc[(j * NPOL + c) * 2] = re;
+                        acc[(j * NPOL + c) * 2 + 1] = im;
+                    }
+                }
+            }
+        }
+        // warp reduction; value index i = (j * NPOL + c) * 2 + re/im
+        if constexpr (NV == 32) {
+            reduce_scatter_step<16>(acc, lane);
+            const int j = lane / (NPOL * 2), v = g + ngp * j;
+            if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (lane % (NPOL * 2))], acc[0]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                for (int o = 16; o; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    const int j = i / (NPOL * 2), v = g + ngp * j;
+                    if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (i % (NPOL * 2))], acc[i]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v < count; v += blockDim.x) {
+            const aw_rec r = a.rec_dg[start + v];
             float2 out[NPOL];
 #pragma unroll
-            for (int c = 0; c < NPOL; ++c) out[c] = make_float2(acc[c].x * a.inv_scale, acc[c].y * a.inv_scale);
+            for (int c = 0; c < NPOL; ++c)
+                out[c] = make_float2(s_out[(v * NPOL + c) * 2] * a.inv_scale,
+                                     s_out[(v * NPOL + c) * 2 + 1] * a.inv_scale);
             if (r.flip) {
 #pragma unroll
                 for (int c = 0; c < NPOL; ++c) out[c].y = -out[c].y;
@@ -339,6 +568,13 @@ __global__ void __launch_bounds__(256, 5) degrid_warp_kernel(DegridArgs a) {
                 dst[0] = out[0];
             }
         }
+    }
+    // visibilities that were not gridded (outside or flagged) predict zero
+    for (int64_t i = a.nvalid + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.nvis;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 *dst = a.vis_out + (int64_t)a.rec[i].orig * NPOL;
+#pragma unroll
+        for (int c = 0; c < NPOL; ++c) dst[c] = make_float2(0.f, 0.f);
     }
 }
 
@@ -358,13 +594,63 @@ int launch_grid_t(const aw_grid_launch &L, const GridArgs &a) {
 
 template <int NPOL, int ST>
 int launch_degrid_t(const DegridArgs &a, int sm_count, cudaStream_t s) {
-    int64_t blocks = (a.nvis + 7) / 8;
-    const int64_t cap = (int64_t)sm_count * 16;
+    int per_sm = 1;
+    AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degrid_items_kernel<NPOL, ST>, 256, 0));
+    int64_t blocks = a.nitems;
+    const int64_t cap = (int64_t)sm_count * std::max(per_sm, 1);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    degrid_warp_kernel<NPOL, ST><<<(unsigned)blocks, 256, 0, s>>>(a);
+    degrid_items_kernel<NPOL, ST><<<(unsigned)blocks, 256, 0, s>>>(a);
     AW_CHECK_LAUNCH();
     return AW_OK;
+}
+
+
+template <int NPOL, int ST>
+int launch_grid_offset_t(const GridOffArgs &a, int sm_count, cudaStream_t s) {
+    // one wave of resident CTAs striding over the items in order, so that the
+    // items in flight share bins and super-tiles (L2 locality)
+    int per_sm = 1;
+    AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_offset_kernel<NPOL, ST>, 256, 0));
+    int64_t blocks = a.nitems;
+    const int64_t cap = (int64_t)sm_count * std::max(per_sm, 1);
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    grid_offset_kernel<NPOL, ST><<<(unsigned)blocks, 256, 0, s>>>(a);
+    AW_CHECK_LAUNCH();
+    return AW_OK;
+}
+
+int launch_grid_offsets(const aw_grid_launch &L) {
+    const aw_plan *p = L.plan;
+    const aw_kernel_set *k = L.kset;
+    GridOffArgs a;
+    a.rec_dg = p->d_rec_dg;
+    a.items = p->d_items_dg;
+    a.nitems = p->nitems_dg;
+    a.ktab = k->d_table;
+    a.bin_offset = k->d_bin_offset;
+    a.bin_support = k->d_bin_support;
+    a.vis = reinterpret_cast<const float2 *>(L.vis);
+    a.weight = L.weight;
+    a.grid = reinterpret_cast<float2 *>(L.grid);
+    a.N = p->N;
+    a.OS = p->OS;
+    a.wsum = p->d_wsum;
+    a.nonfinite = p->d_nonfinite;
+    a.inv_scale = 1.0f / k->scale;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int st = k->spec.storage;
+    if (p->npol == 1) {
+        if (st == AW_STORAGE_FP32) return launch_grid_offset_t<1, AW_STORAGE_FP32>(a, sms, L.stream);
+        if (st == AW_STORAGE_BF16) return launch_grid_offset_t<1, AW_STORAGE_BF16>(a, sms, L.stream);
+        return launch_grid_offset_t<1, AW_STORAGE_FP16>(a, sms, L.stream);
+    }
+    if (st == AW_STORAGE_FP32) return launch_grid_offset_t<4, AW_STORAGE_FP32>(a, sms, L.stream);
+    if (st == AW_STORAGE_BF16) return launch_grid_offset_t<4, AW_STORAGE_BF16>(a, sms, L.stream);
+    return launch_grid_offset_t<4, AW_STORAGE_FP16>(a, sms, L.stream);
 }
 
 }  // namespace
@@ -373,6 +659,7 @@ int aw_launch_grid(const aw_grid_launch &L) {
     const aw_plan *p = L.plan;
     const aw_kernel_set *k = L.kset;
     if (p->nitems == 0) return AW_OK;
+    if (p->tune.grid_mode == AW_GRID_OFFSETS) return launch_grid_offsets(L);
     GridArgs a;
     a.rec = p->d_rec;
     a.items = p->d_items;
@@ -406,6 +693,9 @@ int aw_launch_degrid(const aw_plan *p, const aw_kernel_set *k, const void *grid,
     if (p->nvis == 0) return AW_OK;
     DegridArgs a;
     a.rec = p->d_rec;
+    a.rec_dg = p->d_rec_dg;
+    a.items = p->d_items_dg;
+    a.nitems = p->nitems_dg;
     a.nvis = p->nvis;
     a.nvalid = p->nvalid;
     a.ktab = k->d_table;

@@ -94,7 +94,13 @@ struct aw_plan {
     aw_tune tune{};
     double mean_taps = 0;
     aw_rec *d_rec = nullptr;        // [nvis] sorted (valid first) by (bin, tile, position)
-    int4 *d_items = nullptr;        // [nitems] {start, count, bin, tile}
+    int4 *d_items = nullptr;        // [nitems] {start, count, bin, 0}
+    // degridding order: the valid visibilities by (bin, super-tile, oversampled
+    // offset, position), cut into items of at most AW_DG_CHUNK visibilities
+    aw_rec *d_rec_dg = nullptr;     // [nvalid]
+    int4 *d_items_dg = nullptr;     // [nitems_dg] {start, count, bin, 0}
+    int64_t nitems_dg = 0;
+    int dg_tile = 256;
     int32_t *d_plane_support = nullptr;  // [nw] support per w plane
     std::vector<int32_t> bin_support;
     // grid-time statistics (device): [0] weight sum (double), [1] non-finite count
@@ -109,6 +115,10 @@ struct aw_plan {
     const void *g_vis = nullptr, *g_weight = nullptr, *g_grid = nullptr, *g_kset = nullptr;
     cudaStream_t g_stream = nullptr;
 };
+
+// Visibilities per degridding work item: 8 warps x 4 visibilities.
+constexpr int AW_DG_VB = 4;
+constexpr int AW_DG_CHUNK = 8 * AW_DG_VB;
 
 // ---------------------------------------------------------------- table layout
 // Inside one (bin, fy, fx) block of L = S*S taps, the P Mueller values of a tap

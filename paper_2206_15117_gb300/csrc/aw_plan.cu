@@ -277,6 +277,21 @@ __global__ void rec_orig_kernel(const aw_rec *rec, int64_t n, uint32_t *perm) {
         perm[i] = rec[i].orig;
 }
 
+// Degridding key of the i-th valid visibility (grid order): (bin, super-tile
+// row, super-tile column, fy, fx) above the position inside the super-tile.
+__global__ void dg_key_kernel(const aw_rec *rec, int64_t nv, int OS, int stbits, int nst, uint64_t *keys,
+                              uint32_t *vals) {
+    const int smask = (1 << stbits) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const aw_rec r = rec[i];
+        const uint64_t grp = (((uint64_t)r.bin * nst + (r.y0 >> stbits)) * nst + (r.x0 >> stbits)) * OS * OS +
+                             (uint64_t)r.fy * OS + r.fx;
+        keys[i] = (grp << (2 * stbits)) | ((uint64_t)(r.y0 & smask) << stbits) | (uint64_t)(r.x0 & smask);
+        vals[i] = (uint32_t)i;
+    }
+}
+
 int grid_blocks(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -324,6 +339,66 @@ int fill_coord_args(const aw_vis_desc *vis, const aw_kernel_set *ks, int tile, C
     return AW_OK;
 }
 
+// LSD radix sort of (key, value) pairs over `passes` 8-bit digits; on return
+// k0/v0 point at the sorted arrays.  `counts`/`offs` hold 256 * ceil(n / RS_TILE)
+// words, `scratch` serves the exclusive scan of that many words.
+int radix_sort_pairs(uint64_t *&k0, uint32_t *&v0, uint64_t *&k1, uint32_t *&v1, int64_t n, int passes,
+                     uint32_t *counts, uint32_t *offs, void *scratch, cudaStream_t s) {
+    const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    const int64_t ncounts = (int64_t)256 * ntiles;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = pass * 8;
+        radix_hist_kernel<<<ntiles, RS_THREADS, 0, s>>>(k0, n, shift, counts, ntiles);
+        AW_CHECK_LAUNCH();
+        int rc = aw_exclusive_scan_u32(counts, offs, ncounts, scratch, s);
+        if (rc) return rc;
+        radix_scatter_kernel<<<ntiles, RS_THREADS, 0, s>>>(k0, v0, n, shift, offs, ntiles, k1, v1);
+        AW_CHECK_LAUNCH();
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    return AW_OK;
+}
+
+// Cut the sorted keys of the nv valid visibilities into segments of equal
+// key >> shift and the segments into items of at most `chunk` visibilities;
+// allocates *items.  `flag`/`segid` hold nv + 1 words each.
+int build_items(const uint64_t *keys, int64_t nv, int shift, int chunk, const aw_rec *rec, uint32_t *flag,
+                uint32_t *segid, void *scratch, int4 **items, int64_t *nitems, cudaStream_t s) {
+    seg_flag_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(keys, nv, shift, flag);
+    AW_CHECK_LAUNCH();
+    int rc = aw_exclusive_scan_u32(flag, segid, nv, scratch, s);
+    if (rc) return rc;
+    uint32_t last_id = 0, last_flag = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&last_id, segid + nv - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaMemcpyAsync(&last_flag, flag + nv - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nseg = (int64_t)last_id + last_flag;
+    DevBuf bstarts, bnch, bbase;
+    AW_CUDA_TRY(cudaMalloc(&bstarts.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(cudaMalloc(&bnch.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(cudaMalloc(&bbase.p, sizeof(uint32_t) * nseg));
+    seg_start_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(flag, segid, nv, (uint32_t *)bstarts.p);
+    AW_CHECK_LAUNCH();
+    seg_chunks_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, nseg, (uint32_t)nv, chunk,
+                                                            (uint32_t *)bnch.p);
+    AW_CHECK_LAUNCH();
+    rc = aw_exclusive_scan_u32((uint32_t *)bnch.p, (uint32_t *)bbase.p, nseg, scratch, s);
+    if (rc) return rc;
+    uint32_t lb = 0, ln = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&lb, (uint32_t *)bbase.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaMemcpyAsync(&ln, (uint32_t *)bnch.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    *nitems = (int64_t)lb + ln;
+    AW_CUDA_TRY(cudaMalloc(items, sizeof(int4) * std::max<int64_t>(*nitems, 1)));
+    emit_items_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, (uint32_t *)bbase.p, nseg,
+                                                            (uint32_t)nv, chunk, rec, *items);
+    AW_CHECK_LAUNCH();
+    // the temporaries are freed on return: finish the kernels that read them
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    return AW_OK;
+}
+
 }  // namespace
 
 int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, const aw_tune *tune,
@@ -333,11 +408,17 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
         return aw_set_error(AW_EINVAL, "vis descriptor incomplete");
     if (vis->nvis > 0x7fffffffLL) return aw_set_error(AW_EINVAL, "nvis %lld above 2^31-1", (long long)vis->nvis);
     const aw_kernel_spec &sp = ks->spec;
-    aw_tune t = tune ? *tune : aw_tune{32, 256, 2, 0};
+    aw_tune t = tune ? *tune : aw_tune{32, 256, 2, 0, AW_GRID_TILES};
     if (t.tile < 8 || t.tile > 256 || (t.tile & (t.tile - 1))) return aw_set_error(AW_EINVAL, "tile %d", t.tile);
     if (t.chunk < 32 || t.chunk > 2048) return aw_set_error(AW_EINVAL, "chunk %d", t.chunk);
     if (t.ctas_per_sm < 1 || t.ctas_per_sm > 8) t.ctas_per_sm = 2;
+    if (t.dg_tile == 0) t.dg_tile = 256;
+    if (t.dg_tile < 32 || t.dg_tile > 4096 || (t.dg_tile & (t.dg_tile - 1)))
+        return aw_set_error(AW_EINVAL, "dg_tile %d", t.dg_tile);
+    if (t.grid_mode != AW_GRID_TILES && t.grid_mode != AW_GRID_OFFSETS)
+        return aw_set_error(AW_EINVAL, "grid_mode %d", t.grid_mode);
     plan->tune = t;
+    plan->dg_tile = t.dg_tile;
     plan->nvis = vis->nvis;
     plan->N = sp.N;
     plan->OS = sp.OS;
@@ -394,17 +475,8 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     AW_CUDA_TRY(cudaMalloc(&bscan.p, sizeof(uint32_t) * scan_n));
     AW_CUDA_TRY(cudaMalloc(&bscratch.p, aw_scan_scratch_bytes(scan_n)));
     uint32_t *counts = (uint32_t *)bcounts.p, *offs = (uint32_t *)bscan.p;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int shift = pass * 8;
-        radix_hist_kernel<<<ntiles, RS_THREADS, 0, s>>>(k0, n, shift, counts, ntiles);
-        AW_CHECK_LAUNCH();
-        int rc = aw_exclusive_scan_u32(counts, offs, ncounts, bscratch.p, s);
-        if (rc) return rc;
-        radix_scatter_kernel<<<ntiles, RS_THREADS, 0, s>>>(k0, v0, n, shift, offs, ntiles, k1, v1);
-        AW_CHECK_LAUNCH();
-        std::swap(k0, k1);
-        std::swap(v0, v1);
-    }
+    int rc = radix_sort_pairs(k0, v0, k1, v1, n, passes, counts, offs, bscratch.p, s);
+    if (rc) return rc;
     gather_rec_kernel<<<grid_blocks(n, 256), 256, 0, s>>>((aw_rec *)brec.p, v0, n, plan->d_rec);
     AW_CHECK_LAUNCH();
     unsigned long long hc[4];
@@ -420,37 +492,29 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
         plan->nitems = 0;
         return AW_OK;
     }
-    // segments of equal (bin, tile), then chunks
-    uint32_t *flag = counts, *segid = offs;  // reuse (size >= n + 1)
-    seg_flag_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(k0, nv, 2 * a.tbits, flag);
-    AW_CHECK_LAUNCH();
-    int rc = aw_exclusive_scan_u32(flag, segid, nv, bscratch.p, s);
+    // gridding items: runs of equal (bin, tile), then chunks
+    rc = build_items(k0, nv, 2 * a.tbits, t.chunk, plan->d_rec, counts, offs, bscratch.p, &plan->d_items,
+                     &plan->nitems, s);
     if (rc) return rc;
-    uint32_t last_id = 0, last_flag = 0;
-    AW_CUDA_TRY(cudaMemcpyAsync(&last_id, segid + nv - 1, 4, cudaMemcpyDeviceToHost, s));
-    AW_CUDA_TRY(cudaMemcpyAsync(&last_flag, flag + nv - 1, 4, cudaMemcpyDeviceToHost, s));
-    AW_CUDA_TRY(cudaStreamSynchronize(s));
-    const int64_t nseg = (int64_t)last_id + last_flag;
-    DevBuf bstarts, bnch, bbase;
-    AW_CUDA_TRY(cudaMalloc(&bstarts.p, sizeof(uint32_t) * nseg));
-    AW_CUDA_TRY(cudaMalloc(&bnch.p, sizeof(uint32_t) * nseg));
-    AW_CUDA_TRY(cudaMalloc(&bbase.p, sizeof(uint32_t) * nseg));
-    seg_start_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(flag, segid, nv, (uint32_t *)bstarts.p);
+
+    // degridding order: (bin, super-tile, oversampled offset, position in super-tile)
+    const int stbits = ilog2(plan->dg_tile);
+    const int nst = (sp.N + plan->dg_tile - 1) >> stbits;
+    const uint64_t ngroups = (uint64_t)ks->nbins * nst * nst * sp.OS * sp.OS;
+    const uint64_t dg_maxkey = ngroups << (2 * stbits);
+    int dg_bits = 0;
+    while (dg_bits < 63 && (1ull << dg_bits) <= dg_maxkey) ++dg_bits;
+    if (dg_bits > 62) return aw_set_error(AW_EINVAL, "degridding key needs %d bits; raise dg_tile", dg_bits);
+    dg_key_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(plan->d_rec, nv, sp.OS, stbits, nst, k0, v0);
     AW_CHECK_LAUNCH();
-    seg_chunks_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, nseg, (uint32_t)nv,
-                                                            t.chunk, (uint32_t *)bnch.p);
-    AW_CHECK_LAUNCH();
-    rc = aw_exclusive_scan_u32((uint32_t *)bnch.p, (uint32_t *)bbase.p, nseg, bscratch.p, s);
+    rc = radix_sort_pairs(k0, v0, k1, v1, nv, (dg_bits + 7) / 8, counts, offs, bscratch.p, s);
     if (rc) return rc;
-    uint32_t lb = 0, ln = 0;
-    AW_CUDA_TRY(cudaMemcpyAsync(&lb, (uint32_t *)bbase.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
-    AW_CUDA_TRY(cudaMemcpyAsync(&ln, (uint32_t *)bnch.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
-    AW_CUDA_TRY(cudaStreamSynchronize(s));
-    plan->nitems = (int64_t)lb + ln;
-    AW_CUDA_TRY(cudaMalloc(&plan->d_items, sizeof(int4) * plan->nitems));
-    emit_items_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, (uint32_t *)bbase.p, nseg,
-                                                            (uint32_t)nv, t.chunk, plan->d_rec, plan->d_items);
+    AW_CUDA_TRY(cudaMalloc(&plan->d_rec_dg, sizeof(aw_rec) * nv));
+    gather_rec_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(plan->d_rec, v0, nv, plan->d_rec_dg);
     AW_CHECK_LAUNCH();
+    rc = build_items(k0, nv, 2 * stbits, AW_DG_CHUNK, plan->d_rec_dg, counts, offs, bscratch.p,
+                     &plan->d_items_dg, &plan->nitems_dg, s);
+    if (rc) return rc;
     AW_CUDA_TRY(cudaStreamSynchronize(s));
     return AW_OK;
 }

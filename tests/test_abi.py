@@ -44,10 +44,10 @@ def test_struct_sizes_match_header_layout(lib):
     import ctypes
     from paper_2206_15117_gb300 import aw
     # natural C layout on LP64: checked against the field order of the header
-    assert ctypes.sizeof(aw.aw_tune) == 16
+    assert ctypes.sizeof(aw.aw_tune) == 20
     assert ctypes.sizeof(aw.aw_stats) == 40
     assert ctypes.sizeof(aw.aw_vis_desc) == 8 * 3 + 7 * 8
-    assert ctypes.sizeof(aw.aw_plan_info) == 5 * 8 + 8 + 8
+    assert ctypes.sizeof(aw.aw_plan_info) == 5 * 8 + 8 + 8 + 8
 
 
 def test_last_error_is_empty_string_initially(lib):

@@ -136,11 +136,13 @@ def test_small_chunks_and_tiles_ragged(ctx):
     _check_degrid(c)
 
 
-def test_flags_outside_and_nonfinite(ctx):
+@pytest.mark.parametrize("grid_mode", [0, 1])
+def test_flags_outside_and_nonfinite(ctx, grid_mode):
+    from paper_2206_15117_gb300 import aw
     ob, kw = case_fullpol(N=128, n_t=12)
     rng = np.random.default_rng(4)
     flags = (rng.random(ob.nvis) < 0.05).astype(np.uint8)
-    c = Case(ctx, ob, kw, flags=flags)
+    c = Case(ctx, ob, kw, flags=flags, tune=aw.aw_tune(32, 256, 2, 0, grid_mode))
     bad = np.flatnonzero(c.co.valid == 1)[:5]
     c.vis[bad[0], 1] = np.nan
     c.vis[bad[1], 0] = np.inf
@@ -169,10 +171,12 @@ def test_grid_accumulates_into_existing_grid(cfg1):
 # Mixed precision (kernels in BF16 / FP16, FP32 products and accumulation):
 # the error is set by the 8 (BF16) or 11 (FP16) significand bits of the kernel
 # values; the bounds below are about 2^-9 and 2^-12 relative.
+@pytest.mark.parametrize("grid_mode", [0, 1])
 @pytest.mark.parametrize("storage,tol", [(1, 4e-3), (2, 5e-4)])
-def test_mixed_precision_grid_and_degrid(ctx, storage, tol):
+def test_mixed_precision_grid_and_degrid(ctx, storage, tol, grid_mode):
+    from paper_2206_15117_gb300 import aw
     ob, kw = case_wproj(vis_fraction=0.001)
-    c = Case(ctx, ob, kw, storage=storage)
+    c = Case(ctx, ob, kw, storage=storage, tune=aw.aw_tune(32, 256, 2, 0, grid_mode))
     g, st = c.gpu_grid()
     G, ws, _ = c.oracle_grid()
     l2, mx = rel_err(g, G)
@@ -181,3 +185,58 @@ def test_mixed_precision_grid_and_degrid(ctx, storage, tol):
     v = c.gpu_degrid()
     l2, mx = rel_err(v, c.oracle_degrid())
     assert l2 < tol, (l2, mx)
+
+
+# Degridding visits the visibilities grouped by (bin, super-tile, oversampled
+# offset): the item count is a host-side function of the coordinates, and the
+# result must not depend on the super-tile size.
+@pytest.mark.parametrize("dg_tile", [32, 4096])
+def test_degrid_super_tile_groups(ctx, dg_tile):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=12)
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, dg_tile, 0))
+    _check_degrid(c)
+    co, OS = c.co, kw["OS"]
+    ok = co.valid == 1
+    b = int(np.log2(dg_tile))
+    grp = np.stack([co.bin[ok], co.y0[ok] >> b, co.x0[ok] >> b, co.fy[ok] * OS + co.fx[ok]], axis=1)
+    _, cnt = np.unique(grp, axis=0, return_counts=True)
+    info = aw.aw_plan_query(c.plan)
+    assert info.nitems_degrid == int(((cnt + 31) // 32).sum())
+    assert info.nitems_degrid >= len(cnt)
+
+
+def test_degrid_rejects_bad_super_tile(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(N=128, n_t=4)
+    kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
+    vd, _keep = aw.device_observation(ob)
+    with pytest.raises(RuntimeError, match="dg_tile"):
+        aw.aw_plan_create(ctx, vd, kg, tune=aw.aw_tune(32, 256, 2, 48, 0))
+    with pytest.raises(RuntimeError, match="grid_mode"):
+        aw.aw_plan_create(ctx, vd, kg, tune=aw.aw_tune(32, 256, 2, 0, 7))
+
+
+# The offset-grouped gridding schedule against the same oracle: Stokes I,
+# w-projection and full-polarisation AW cases, direct and graph-captured,
+# with small and large super-tiles.
+@pytest.mark.parametrize("which,dg_tile", [("cfg1", 256), ("wproj", 32), ("fullpol", 256), ("fullpol", 4096)])
+def test_offset_schedule_grid(ctx, which, dg_tile):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = {"cfg1": case_stokes_i_cfg1, "wproj": lambda: case_wproj(vis_fraction=0.002),
+              "fullpol": case_fullpol}[which]()
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, dg_tile, aw.AW_GRID_OFFSETS))
+    _check_grid(c)
+    _check_grid(c, batched=True)
+
+
+def test_autotune_returns_a_valid_schedule(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=12)
+    kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
+    vd, _keep = aw.device_observation(ob)
+    t = aw.aw_autotune(ctx, vd, kg)
+    assert t.grid_mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS)
+    assert t.tile in (16, 32, 64) and t.chunk in (128, 256, 512)
+    if t.grid_mode == aw.AW_GRID_OFFSETS:
+        assert t.dg_tile in (256, 1024)
