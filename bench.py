@@ -478,7 +478,8 @@ def run_ours(args, rank, world, dist):
     flops = 128.0 * info.mean_taps * info.nvalid          # 16 complex MACs x 8 flop per tap
     g_ms, d_ms = statistics.mean(t_grid), statistics.mean(t_deg)
     dom_ms = max(g_ms, d_ms)
-    dom = "aw_grid (persistent gridding kernel)" if g_ms >= d_ms else "aw_degrid (warp-per-visibility)"
+    gname = "grid_offset_kernel" if tune.grid_mode == aw.AW_GRID_OFFSETS else "grid_persistent_kernel"
+    dom = ("aw_grid (%s)" % gname) if g_ms >= d_ms else "aw_degrid (degrid_items_kernel)"
     peak_tflops = fp32_peak_tflops()
     achieved = flops / (dom_ms / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

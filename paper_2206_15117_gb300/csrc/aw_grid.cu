@@ -432,141 +432,238 @@ __device__ __forceinline__ void reduce_scatter_step(float *x, int lane) {
     if constexpr (H > 1) reduce_scatter_step<H / 2>(x, lane);
 }
 
-// One CTA per work item: up to AW_DG_CHUNK visibilities that share the bin
-// and the oversampled offset (fy, fx), hence one kernel block of S*S taps.
-// The block is staged in shared memory in slabs of DG_TS taps (converted to
-// FP32) and applied to every visibility of the item, so the kernel table is
-// read once per item instead of once per visibility.  The visibilities are
-// dealt to ngp warp groups (v = g + ngp * j, j < AW_DG_VB); the warps of a
-// group split the taps; lanes stride over taps and hold AW_DG_VB x NPOL
-// complex partial sums, reduced over the warp and then across the group's
-// warps in shared memory.
+// Kernel-table chunk geometry of one tap: NCH chunks of CB bytes each (the
+// 16-byte chunks of aw_tab_index, or one element when P == 1).
+template <int P, int ST>
+struct TabChunks {
+    static constexpr int EB = (ST == AW_STORAGE_FP32) ? 8 : 4;   // bytes per complex value
+    static constexpr int CE = (P == 1) ? 1 : 16 / EB;            // complex values per chunk
+    static constexpr int CB = CE * EB;                           // bytes per chunk
+    static constexpr int NCH = P / CE;                           // chunks per tap
+    static constexpr int SLAB_BYTES = DG_TS * NCH * CB;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+template <int CB>
+__device__ __forceinline__ void cp_async_chunk(uint32_t dst, const void *src) {
+    if constexpr (CB == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(src), "n"(CB) : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Mueller row c (values c*NPOL .. c*NPOL+NPOL-1) of tap tl from a staged slab.
+template <int NPOL, int ST>
+__device__ __forceinline__ void smem_krow(const char *slab, int tl, int c, float2 (&k)[NPOL]) {
+    using TC = TabChunks<NPOL * NPOL, ST>;
+    if constexpr (NPOL == 1) {
+        if constexpr (ST == AW_STORAGE_FP32) {
+            k[0] = reinterpret_cast<const float2 *>(slab)[tl];
+        } else {
+            const uint32_t w = reinterpret_cast<const uint32_t *>(slab)[tl];
+            if constexpr (ST == AW_STORAGE_BF16) k[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+            else k[0] = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        }
+    } else if constexpr (ST == AW_STORAGE_FP32) {
+        // row c = chunks 2c and 2c+1 (two complex values each)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 q = reinterpret_cast<const float4 *>(slab)[(2 * c + h) * DG_TS + tl];
+            k[2 * h] = make_float2(q.x, q.y);
+            k[2 * h + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+        // row c = chunk c (four complex values)
+        const uint4 q = reinterpret_cast<const uint4 *>(slab)[c * DG_TS + tl];
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if constexpr (ST == AW_STORAGE_BF16) k[j] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[j]));
+            else k[j] = __half22float2(*reinterpret_cast<const __half2 *>(&w[j]));
+        }
+    }
+    (void)sizeof(TC);
+}
+
+// One CTA works through the items b, b + gridDim.x, ... (up to AW_DG_CHUNK
+// visibilities that share the bin and the oversampled offset (fy, fx), hence
+// one kernel block of S*S taps).  The block is staged in shared memory in
+// slabs of DG_TS taps, in the table's own storage format, with cp.async into
+// two buffers: the next slab (of this item or the next) streams in while the
+// current one is used.  The visibilities are dealt to ngp warp groups
+// (v = g + ngp * j, j < AW_DG_VB); the warps of a group split the taps; lanes
+// stride over taps, load the npol grid values of their taps for every
+// visibility first, then apply the kernel one Mueller row at a time.  Partial
+// sums (AW_DG_VB x NPOL complex per lane) are reduce-scattered over the warp
+// and summed across the group's warps in shared memory.
 template <int NPOL, int ST>
 __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
     constexpr int P = NPOL * NPOL;
     constexpr int VB = AW_DG_VB;
     constexpr int NV = VB * NPOL * 2;  // partial sums per lane
-    __shared__ __align__(16) float2 s_k[DG_TS * P];
-    __shared__ float s_out[AW_DG_CHUNK * NPOL * 2];
+    using TC = TabChunks<P, ST>;
+    extern __shared__ __align__(16) char dsm[];
+    float *s_out = reinterpret_cast<float *>(dsm + 2 * TC::SLAB_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t plane = (int64_t)a.N * a.N;
-    for (int64_t item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const float2 *gplane[NPOL];
+#pragma unroll
+    for (int s2 = 0; s2 < NPOL; ++s2) gplane[s2] = a.grid + (int64_t)s2 * a.N * a.N;
+    const char *ktab = reinterpret_cast<const char *>(a.ktab);
+
+    // ---- staging of (item, slab) into buffer b
+    auto stage = [&](int64_t item, int slab, int b) {
         const int4 it = a.items[item];
-        const int start = it.x, count = it.y, bin = it.z;
-        const int S = a.bin_support[bin];
+        const int S = a.bin_support[it.z];
         const int L = S * S;
-        const float invS = 1.0f / (float)S;
-        const aw_rec r0 = a.rec_dg[start];
-        const int64_t kbase = a.bin_offset[bin] + (int64_t)(r0.fy * a.OS + r0.fx) * L * P;
-        const int need = (count + VB - 1) / VB;
-        const int ngp = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
-        const int wpg = 8 / ngp;
-        const int g = warp & (ngp - 1), ph = warp / ngp;
-        const float2 *gb[VB];
-        bool has[VB];
-#pragma unroll
-        for (int j = 0; j < VB; ++j) {
-            const int v = g + ngp * j;
-            has[j] = v < count;
-            const aw_rec r = has[j] ? a.rec_dg[start + v] : r0;
-            gb[j] = a.grid + (int64_t)r.y0 * a.N + r.x0;
+        const aw_rec r0 = a.rec_dg[it.x];
+        const int64_t kbase = a.bin_offset[it.z] + (int64_t)(r0.fy * a.OS + r0.fx) * L * P;  // complex index
+        const char *src = ktab + kbase * TC::EB;
+        const int t0 = slab * DG_TS;
+        const int ns = min(DG_TS, L - t0);
+        const uint32_t dst = smem_u32(dsm) + (uint32_t)(b * TC::SLAB_BYTES);
+        for (int idx = threadIdx.x; idx < ns * TC::NCH; idx += blockDim.x) {
+            const int c = idx / ns, tl = idx - c * ns;
+            cp_async_chunk<TC::CB>(dst + (uint32_t)((c * DG_TS + tl) * TC::CB),
+                                   src + ((int64_t)c * L + t0 + tl) * TC::CB);
         }
+        cp_async_commit();
+    };
+    auto nslabs = [&](int64_t item) {
+        const int S = a.bin_support[a.items[item].z];
+        return (S * S + DG_TS - 1) / DG_TS;
+    };
+
+    int64_t item = blockIdx.x;
+    if (item < a.nitems) {
+        int slab = 0, nsl = nslabs(item), buf = 0;
+        stage(item, 0, 0);
+        // per-item state
+        int start = 0, count = 0, S = 0, L = 0, ngp = 1, wpg = 8, g = 0, ph = 0;
+        float invS = 1.f;
+        uint32_t goff[VB];  // y0 * N + x0 (< 2^32: coordinates are 16-bit)
+        bool has[VB];
         float acc[NV];
+        for (;;) {
+            if (slab == 0) {
+                const int4 it = a.items[item];
+                start = it.x; count = it.y;
+                S = a.bin_support[it.z];
+                L = S * S;
+                invS = 1.0f / (float)S;
+                const int need = (count + VB - 1) / VB;
+                ngp = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
+                wpg = 8 / ngp;
+                g = warp & (ngp - 1);
+                ph = warp / ngp;
 #pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = 0.f;
-        __syncthreads();  // the previous item has finished with s_out and s_k
-        for (int i = threadIdx.x; i < count * NPOL * 2; i += blockDim.x) s_out[i] = 0.f;
-        for (int t0 = 0; t0 < L; t0 += DG_TS) {
-            const int ns = min(DG_TS, L - t0);
-            __syncthreads();
-            for (int tl = threadIdx.x; tl < ns; tl += blockDim.x) {
-                float2 k[P];
-                load_k<ST, P>(a.ktab, kbase, L, t0 + tl, k);
-                if constexpr (P % 2 == 0) {
-#pragma unroll
-                    for (int c = 0; c < P / 2; ++c)
-                        reinterpret_cast<float4 *>(s_k)[c * DG_TS + tl] =
-                            make_float4(k[2 * c].x, k[2 * c].y, k[2 * c + 1].x, k[2 * c + 1].y);
-                } else {
-                    s_k[tl] = k[0];
+                for (int j = 0; j < VB; ++j) {
+                    const int v = g + ngp * j;
+                    has[j] = v < count;
+                    const aw_rec r = a.rec_dg[start + (has[j] ? v : 0)];
+                    goff[j] = (uint32_t)r.y0 * (uint32_t)a.N + r.x0;
                 }
+#pragma unroll
+                for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+                for (int i = threadIdx.x; i < count * NPOL * 2; i += blockDim.x) s_out[i] = 0.f;
+            }
+            // the next (item, slab) streams into the other buffer
+            int64_t nitem = item;
+            int nslab = slab + 1, nnsl = nsl;
+            if (nslab == nsl) { nitem = item + gridDim.x; nslab = 0; nnsl = nitem < a.nitems ? nslabs(nitem) : 0; }
+            const bool has_next = nitem < a.nitems;
+            if (has_next) {
+                stage(nitem, nslab, buf ^ 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
+            const char *sl = dsm + buf * TC::SLAB_BYTES;
+            const int t0 = slab * DG_TS;
+            const int ns = min(DG_TS, L - t0);
             for (int tl = ph * 32 + lane; tl < ns; tl += wpg * 32) {
                 const int t = t0 + tl;
                 const int jy = (int)(((float)t + 0.5f) * invS);
-                const int toff = jy * a.N + (t - jy * S);
-                float2 k[P];
-                if constexpr (P % 2 == 0) {
-#pragma unroll
-                    for (int c = 0; c < P / 2; ++c) {
-                        const float4 q = reinterpret_cast<const float4 *>(s_k)[c * DG_TS + tl];
-                        k[2 * c] = make_float2(q.x, q.y);
-                        k[2 * c + 1] = make_float2(q.z, q.w);
-                    }
-                } else {
-                    k[0] = s_k[tl];
-                }
+                const uint32_t toff = (uint32_t)(jy * a.N + (t - jy * S));
+                float2 gv[VB][NPOL];
 #pragma unroll
                 for (int j = 0; j < VB; ++j) {
-                    if (!has[j]) continue;
-                    float2 gv[NPOL];
 #pragma unroll
-                    for (int s = 0; s < NPOL; ++s) gv[s] = __ldg(gb[j] + toff + s * plane);
+                    for (int s2 = 0; s2 < NPOL; ++s2)
+                        gv[j][s2] = has[j] ? __ldg(gplane[s2] + (goff[j] + toff)) : make_float2(0.f, 0.f);
+                }
 #pragma unroll
-                    for (int c = 0; c < NPOL; ++c) {
+                for (int c = 0; c < NPOL; ++c) {
+                    float2 kr[NPOL];
+                    smem_krow<NPOL, ST>(sl, tl, c, kr);
+#pragma unroll
+                    for (int j = 0; j < VB; ++j) {
                         float re = acc[(j * NPOL + c) * 2], im = acc[(j * NPOL + c) * 2 + 1];
 #pragma unroll
-                        for (int s = 0; s < NPOL; ++s) {
-                            const float2 kk = k[c * NPOL + s];
-                            re = fmaf(kk.x, gv[s].x, re);
-                            re = fmaf(-kk.y, gv[s].y, re);
-                            im = fmaf(kk.x, gv[s].y, im);
-                            im = fmaf(kk.y, gv[s].x, im);
+                        for (int s2 = 0; s2 < NPOL; ++s2) {
+                            re = fmaf(kr[s2].x, gv[j][s2].x, re);
+                            re = fmaf(-kr[s2].y, gv[j][s2].y, re);
+                            im = fmaf(kr[s2].x, gv[j][s2].y, im);
+                            im = fmaf(kr[s2].y, gv[j][s2].x, im);
                         }
                         acc[(j * NPOL + c) * 2] = re;
                         acc[(j * NPOL + c) * 2 + 1] = im;
                     }
                 }
             }
-        }
-        // warp reduction; value index i = (j * NPOL + c) * 2 + re/im
-        if constexpr (NV == 32) {
-            reduce_scatter_step<16>(acc, lane);
-            const int j = lane / (NPOL * 2), v = g + ngp * j;
-            if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (lane % (NPOL * 2))], acc[0]);
-        } else {
+            if (slab == nsl - 1) {
+                // warp reduction; value index i = (j * NPOL + c) * 2 + re/im
+                if constexpr (NV == 32) {
+                    reduce_scatter_step<16>(acc, lane);
+                    const int j = lane / (NPOL * 2), v = g + ngp * j;
+                    if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (lane % (NPOL * 2))], acc[0]);
+                } else {
 #pragma unroll
-            for (int i = 0; i < NV; ++i)
-                for (int o = 16; o; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-            if (lane == 0) {
+                    for (int i = 0; i < NV; ++i)
+                        for (int o = 16; o; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+                    if (lane == 0) {
 #pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    const int j = i / (NPOL * 2), v = g + ngp * j;
-                    if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (i % (NPOL * 2))], acc[i]);
+                        for (int i = 0; i < NV; ++i) {
+                            const int j = i / (NPOL * 2), v = g + ngp * j;
+                            if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (i % (NPOL * 2))], acc[i]);
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int v = threadIdx.x; v < count; v += blockDim.x) {
+                    const aw_rec r = a.rec_dg[start + v];
+                    float2 out[NPOL];
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c)
+                        out[c] = make_float2(s_out[(v * NPOL + c) * 2] * a.inv_scale,
+                                             s_out[(v * NPOL + c) * 2 + 1] * a.inv_scale);
+                    if (r.flip) {
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c) out[c].y = -out[c].y;
+                        if (NPOL == 4) { float2 t = out[1]; out[1] = out[2]; out[2] = t; }
+                    }
+                    float2 *dst = a.vis_out + (int64_t)r.orig * NPOL;
+                    if constexpr (NPOL == 4) {
+                        reinterpret_cast<float4 *>(dst)[0] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+                        reinterpret_cast<float4 *>(dst)[1] = make_float4(out[2].x, out[2].y, out[3].x, out[3].y);
+                    } else {
+                        dst[0] = out[0];
+                    }
                 }
             }
-        }
-        __syncthreads();
-        for (int v = threadIdx.x; v < count; v += blockDim.x) {
-            const aw_rec r = a.rec_dg[start + v];
-            float2 out[NPOL];
-#pragma unroll
-            for (int c = 0; c < NPOL; ++c)
-                out[c] = make_float2(s_out[(v * NPOL + c) * 2] * a.inv_scale,
-                                     s_out[(v * NPOL + c) * 2 + 1] * a.inv_scale);
-            if (r.flip) {
-#pragma unroll
-                for (int c = 0; c < NPOL; ++c) out[c].y = -out[c].y;
-                if (NPOL == 4) { float2 t = out[1]; out[1] = out[2]; out[2] = t; }
-            }
-            float2 *dst = a.vis_out + (int64_t)r.orig * NPOL;
-            if constexpr (NPOL == 4) {
-                reinterpret_cast<float4 *>(dst)[0] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
-                reinterpret_cast<float4 *>(dst)[1] = make_float4(out[2].x, out[2].y, out[3].x, out[3].y);
-            } else {
-                dst[0] = out[0];
-            }
+            __syncthreads();  // buffer `buf` and s_out are free again
+            if (!has_next) break;
+            item = nitem;
+            slab = nslab;
+            nsl = nnsl;
+            buf ^= 1;
         }
     }
     // visibilities that were not gridded (outside or flagged) predict zero
@@ -576,6 +673,11 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
 #pragma unroll
         for (int c = 0; c < NPOL; ++c) dst[c] = make_float2(0.f, 0.f);
     }
+}
+
+template <int NPOL, int ST>
+size_t degrid_smem_bytes() {
+    return 2 * (size_t)TabChunks<NPOL * NPOL, ST>::SLAB_BYTES + sizeof(float) * AW_DG_CHUNK * NPOL * 2;
 }
 
 template <int NPOL, int ST>
@@ -594,13 +696,16 @@ int launch_grid_t(const aw_grid_launch &L, const GridArgs &a) {
 
 template <int NPOL, int ST>
 int launch_degrid_t(const DegridArgs &a, int sm_count, cudaStream_t s) {
+    const size_t smem = degrid_smem_bytes<NPOL, ST>();
+    AW_CUDA_TRY(cudaFuncSetAttribute(degrid_items_kernel<NPOL, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
     int per_sm = 1;
-    AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degrid_items_kernel<NPOL, ST>, 256, 0));
+    AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degrid_items_kernel<NPOL, ST>, 256, smem));
     int64_t blocks = a.nitems;
     const int64_t cap = (int64_t)sm_count * std::max(per_sm, 1);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    degrid_items_kernel<NPOL, ST><<<(unsigned)blocks, 256, 0, s>>>(a);
+    degrid_items_kernel<NPOL, ST><<<(unsigned)blocks, 256, smem, s>>>(a);
     AW_CHECK_LAUNCH();
     return AW_OK;
 }
