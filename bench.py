@@ -482,8 +482,16 @@ def run_ours(args, rank, world, dist):
     dom = ("aw_grid (%s)" % gname) if g_ms >= d_ms else "aw_degrid (degrid_items_kernel)"
     peak_tflops = fp32_peak_tflops()
     achieved = flops / (dom_ms / 1e3) / 1e12
+    # DRAM bytes per launch of the dominant kernel, from the one-pass ncu capture summarised in
+    # profiles/dram_traffic_fullpol_aw_64M.md (same kernels, this workload, FP32 tables); null otherwise
+    measured_traffic = {("grid_persistent_kernel", 63851035, 64, 128, 1024): 149.65e9,
+                        ("degrid_items_kernel", 63851035, 64, 128, 1024): 14.71e9}
+    dom_kernel = (gname if g_ms >= d_ms else "degrid_items_kernel", int(nvis), tune.tile, tune.chunk,
+                  tune.dg_tile or 1024)
+    traffic = measured_traffic.get(dom_kernel) if not args.subset else None
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
+            "frac": achieved / peak_tflops, "traffic": traffic,
+            "traffic_source": "profiles/dram_traffic_fullpol_aw_64M.md" if traffic else None,
             "peak_source": "FP32 CUDA-core peak derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "flops_per_launch": flops}
 
@@ -563,7 +571,7 @@ def run_ours(args, rank, world, dist):
                            "reasons": clocks["reasons"]},
                 "gpu_launches": launches_per_step * args.steps,
                 "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm,
-                         "dg_tile": tune.dg_tile or 256, "degrid_items": info.nitems_degrid,
+                         "dg_tile": tune.dg_tile or 1024, "degrid_items": info.nitems_degrid,
                          "grid_schedule": ["tiles", "offsets"][tune.grid_mode]},
                 "learned": learned}
         print(json.dumps(line), flush=True)

@@ -121,7 +121,7 @@ typedef struct aw_tune {
     int32_t chunk;           /* max visibilities per work item, 32..2048          */
     int32_t ctas_per_sm;     /* persistent launch: CTAs per SM, 1..8              */
     int32_t dg_tile;         /* degridding super-tile side (power of 2, 32..4096);
-                              * 0 selects 256.  Degridding visits visibilities
+                              * 0 selects 1024.  Degridding visits visibilities
                               * grouped by (bin, super-tile, oversampled offset) */
     int32_t grid_mode;       /* AW_GRID_TILES or AW_GRID_OFFSETS (below)           */
 } aw_tune;
@@ -270,8 +270,9 @@ int aw_grid(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const v
  *
  * then V = P conj(V') for flipped visibilities.  grid: device complex64
  * [npol][N][N]; vis_out: device complex64 [nvis][npol] in the caller's order,
- * OVERWRITTEN (zero for visibilities the plan does not grid).  One warp per
- * visibility; FP32 products, warp-shuffle reduction.
+ * OVERWRITTEN (zero for visibilities the plan does not grid).  Visibilities
+ * that share a bin, a super-tile and an oversampled offset share one kernel
+ * block staged in shared memory; FP32 products, warp reductions.
  */
 int aw_degrid(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const void *grid,
               void *vis_out, void *stream);

@@ -100,7 +100,7 @@ struct aw_plan {
     aw_rec *d_rec_dg = nullptr;     // [nvalid]
     int4 *d_items_dg = nullptr;     // [nitems_dg] {start, count, bin, 0}
     int64_t nitems_dg = 0;
-    int dg_tile = 256;
+    int dg_tile = 1024;
     int32_t *d_plane_support = nullptr;  // [nw] support per w plane
     std::vector<int32_t> bin_support;
     // grid-time statistics (device): [0] weight sum (double), [1] non-finite count

@@ -412,7 +412,7 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     if (t.tile < 8 || t.tile > 256 || (t.tile & (t.tile - 1))) return aw_set_error(AW_EINVAL, "tile %d", t.tile);
     if (t.chunk < 32 || t.chunk > 2048) return aw_set_error(AW_EINVAL, "chunk %d", t.chunk);
     if (t.ctas_per_sm < 1 || t.ctas_per_sm > 8) t.ctas_per_sm = 2;
-    if (t.dg_tile == 0) t.dg_tile = 256;
+    if (t.dg_tile == 0) t.dg_tile = 1024;
     if (t.dg_tile < 32 || t.dg_tile > 4096 || (t.dg_tile & (t.dg_tile - 1)))
         return aw_set_error(AW_EINVAL, "dg_tile %d", t.dg_tile);
     if (t.grid_mode != AW_GRID_TILES && t.grid_mode != AW_GRID_OFFSETS)
