@@ -440,6 +440,101 @@ int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, flo
 int mosaic_gamma_noalloc(const float *beams, int32_t nfield, int32_t N, float eps, float *gamma,
                          void *stream);
 
+/* ---- cleaning: Cotton-Schwab major cycles, Hogbom minor cycle ---------------
+ *
+ * Sec. 2.1: the imager cleans with the Cotton-Schwab algorithm, controlled by
+ * the number of clean cycles, the loop gain, the cycle factor and a threshold;
+ * Sec. 4 names Hogbom cleaning as the iterative part.  A major cycle grids the
+ * residual visibilities, makes the residual image, runs the minor cycle on it,
+ * predicts the model (image -> grid -> degrid) and subtracts it from the
+ * observed visibilities.  Readings (the paper does not write the steps out):
+ * the minor cycle picks the peak of |I| in the clean window (ties to the
+ * lowest row-major pixel index), takes gain x the residual of every Stokes
+ * plane there as the component, and subtracts it with a square patch of the
+ * point-spread function of half-width patch_half, in FP32 with one rounding
+ * per multiply and per subtraction; the cycle threshold is max(threshold,
+ * cycle_factor * sidelobe * peak); the point-spread function is the Stokes I
+ * image of unit Stokes I visibilities, divided by its value at the phase
+ * centre; sidelobe is its largest |value| outside the main lobe, a disk of
+ * radius r0 = the first x > 0 with psf[N/2][N/2 + x] <= 0, and within N/4
+ * pixels of the centre on both axes (with A-projection the outer image of
+ * unit visibilities carries the inverse beam and the grid correction).
+ */
+typedef struct aw_clean_cfg {
+    int32_t n_major;         /* major cycles, >= 1                                */
+    int32_t max_minor;       /* Hogbom iterations per major cycle, >= 0           */
+    float gain;              /* loop gain, (0, 1]                                 */
+    float threshold;         /* stop when the peak |I| of the residual is below   */
+    float cycle_factor;      /* see above; >= 0                                   */
+    int32_t patch_half;      /* point-spread-function patch half-width, [0, N/2)  */
+    int32_t window[4];       /* clean window x0, y0, x1, y1 (half-open), inside
+                              * the image; all zero selects the inner half       */
+} aw_clean_cfg;
+
+typedef struct aw_clean_report {
+    int32_t n_major;         /* major cycles that ran a minor cycle               */
+    int32_t n_minor;         /* Hogbom iterations over all cycles                 */
+    float peak_first;        /* peak |I| in the window of the first residual image */
+    float peak_last;         /* the same for the final residual image             */
+    float sidelobe;          /* point-spread-function sidelobe level              */
+    float reserved;
+    double weight_sum;       /* sum of the gridding weights (aw_stats.weight_sum) */
+} aw_clean_report;
+
+/*
+ * aw_image_to_grid - model image -> uv grid for degridding (the adjoint of the
+ * image step of aw_fft_to_image): divide by the grid correction (zero on row
+ * and column 0), then G(g) = sum_q I(q) exp(-2 pi i (g - N/2)(q - N/2) / N) per
+ * plane, no scaling.  image: device float [npol][N][N]; grid: device complex64
+ * [npol][N][N], overwritten.  kset supplies N, npol and the taper width.
+ */
+int aw_image_to_grid(aw_ctx *ctx, const aw_kernel_set *kset, const float *image, void *grid, void *stream);
+
+/*
+ * aw_degrid_subtract - vis_out = vis - aw_degrid(grid): the residual
+ * visibilities of a major cycle in one pass.  vis, vis_out: device complex64
+ * [nvis][npol] in the caller's order; vis_out may be vis.  Visibilities the
+ * plan does not grid keep vis.
+ */
+int aw_degrid_subtract(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const void *grid,
+                       const void *vis, void *vis_out, void *stream);
+
+/*
+ * aw_psf_sidelobe - the sidelobe level defined above.  psf: device float
+ * [N][N]; *sidelobe: host.  Synchronises `stream`.
+ */
+int aw_psf_sidelobe(aw_ctx *ctx, const float *psf, int32_t N, float *sidelobe, void *stream);
+
+/*
+ * aw_hogbom - Hogbom minor cycle (readings above) until the peak |I| in the
+ * window is below `threshold` or max_iter components are taken.  residual:
+ * device float [npol][N][N], updated in place; psf: device float [N][N] with
+ * its peak at (N/2, N/2); model: device float [npol][N][N], components added;
+ * window: host int32[4] (x0, y0, x1, y1, half-open, non-empty, inside the
+ * image).  One CTA runs the loop; the peak search keeps the maximum of each
+ * 64 x 64 tile (or larger, at most 64 x 64 tiles) and rescans only the tiles a
+ * subtraction touched.  *n_iter: host.  Synchronises `stream`.
+ */
+int aw_hogbom(aw_ctx *ctx, float *residual, const float *psf, int32_t npol, int32_t N, float gain,
+              float threshold, int32_t max_iter, int32_t patch_half, const int32_t *window, float *model,
+              int32_t *n_iter, void *stream);
+
+/*
+ * aw_clean - Cotton-Schwab cleaning of the plan's visibilities.  kgrid /
+ * kdegrid: the plan's GRID and DEGRID kernel sets; vis: device complex64
+ * [nvis][npol]; weight: device float [nvis][npol] or NULL.  Outputs (device,
+ * overwritten): model float [npol][N][N], residual float [npol][N][N] (the
+ * residual image after the last cycle), psf float [N][N].  report: host.
+ * Allocates, and frees before returning, one visibility-sized buffer and one
+ * grid.  Major cycle: stop if the residual peak is below cfg->threshold,
+ * otherwise aw_hogbom down to the cycle threshold, then aw_image_to_grid and
+ * aw_degrid_subtract.  Gridding goes through aw_grid_batched (the plan's
+ * cached graph).  Synchronises `stream` once per major cycle.
+ */
+int aw_clean(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kgrid, const aw_kernel_set *kdegrid,
+             const void *vis, const float *weight, const aw_clean_cfg *cfg, float *model, float *residual,
+             float *psf, aw_clean_report *report, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,9 +22,12 @@ the textbook method with these readings:
   same weights and kernels, divided by its value at the phase centre.
 * Cycle threshold: max(threshold, cycle_factor * sidelobe * peak), with peak the
   largest |I| of the residual in the window at the start of the major cycle and
-  sidelobe the largest |psf| outside the main lobe.  The main lobe is the disk
-  around the centre whose radius r0 is the first pixel distance x > 0 along +l
-  with psf[c][c + x] <= 0 (c = N / 2).
+  sidelobe the largest |psf| outside the main lobe and within N/4 pixels of the
+  centre on both axes (|dx|, |dy| < N/4).  The main lobe is the disk around the
+  centre whose radius r0 is the first pixel distance x > 0 along +l with
+  psf[c][c + x] <= 0 (c = N / 2).  The N/4 limit keeps the outer image out of
+  the level: with A-projection the image of unit visibilities carries the
+  inverse beam and the grid correction, which grow towards the edge.
 * Major cycle k: residual image from the residual visibilities; stop when its
   peak is below the threshold; otherwise run the minor cycle, predict the model
   (image -> grid -> degrid) and subtract it from the observed visibilities.
@@ -44,7 +47,7 @@ def default_window(N: int) -> Tuple[int, int, int, int]:
 
 
 def psf_sidelobe(psf: np.ndarray) -> np.float32:
-    """Largest |psf| outside the main lobe (see the module docstring)."""
+    """Largest |psf| outside the main lobe, |dx|, |dy| < N/4 (module docstring)."""
     psf = np.asarray(psf, dtype=np.float32)
     N = psf.shape[0]
     c = N // 2
@@ -54,7 +57,7 @@ def psf_sidelobe(psf: np.ndarray) -> np.float32:
             r0 = x
             break
     qy, qx = np.mgrid[0:N, 0:N]
-    outside = (qx - c) ** 2 + (qy - c) ** 2 > r0 * r0
+    outside = ((qx - c) ** 2 + (qy - c) ** 2 > r0 * r0) & (np.abs(qx - c) < N // 4) & (np.abs(qy - c) < N // 4)
     if not outside.any():
         return np.float32(0.0)
     return np.float32(np.abs(psf[outside]).max())

@@ -54,6 +54,17 @@ class aw_plan_info(ctypes.Structure):
                 ("nitems_degrid", c_i64)]
 
 
+class aw_clean_cfg(ctypes.Structure):
+    _fields_ = [("n_major", c_i32), ("max_minor", c_i32), ("gain", ctypes.c_float), ("threshold", ctypes.c_float),
+                ("cycle_factor", ctypes.c_float), ("patch_half", c_i32), ("window", c_i32 * 4)]
+
+
+class aw_clean_report(ctypes.Structure):
+    _fields_ = [("n_major", c_i32), ("n_minor", c_i32), ("peak_first", ctypes.c_float),
+                ("peak_last", ctypes.c_float), ("sidelobe", ctypes.c_float), ("reserved", ctypes.c_float),
+                ("weight_sum", c_dbl)]
+
+
 class aw_stats(ctypes.Structure):
     _fields_ = [("n_gridded", c_i64), ("n_outside", c_i64), ("n_flagged", c_i64),
                 ("n_nonfinite", c_i64), ("weight_sum", c_dbl)]
@@ -82,6 +93,13 @@ SIGNATURES = {
     "aw_fft_to_image": (ctypes.c_int, [c_p, c_p, c_p, c_dbl, c_p, c_p]),
     "mosaic_gamma": (ctypes.c_int, [c_p, c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
+    "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
+    "aw_degrid_subtract": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "aw_psf_sidelobe": (ctypes.c_int, [c_p, c_p, c_i32, ctypes.POINTER(ctypes.c_float), c_p]),
+    "aw_hogbom": (ctypes.c_int, [c_p, c_p, c_p, c_i32, c_i32, ctypes.c_float, ctypes.c_float, c_i32, c_i32,
+                                 ctypes.POINTER(c_i32), c_p, ctypes.POINTER(c_i32), c_p]),
+    "aw_clean": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, ctypes.POINTER(aw_clean_cfg), c_p, c_p, c_p,
+                                ctypes.POINTER(aw_clean_report), c_p]),
     "aw_surrogate_create": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(c_p)]),
     "aw_surrogate_destroy": (ctypes.c_int, [c_p]),
     "aw_surrogate_nparams": (ctypes.c_int, [c_p, ctypes.POINTER(c_i64)]),
@@ -338,6 +356,45 @@ def mosaic_gamma_noalloc(beams, eps: float, gamma, stream=None):
     nfield, N = int(beams.shape[0]), int(beams.shape[-1])
     _check(load().mosaic_gamma_noalloc(_ptr(beams), nfield, N, ctypes.c_float(eps), _ptr(gamma),
                                        _stream(stream)), "mosaic_gamma_noalloc")
+
+
+def aw_image_to_grid(ctx: Handle, kset: Handle, image, grid, stream=None):
+    _check(load().aw_image_to_grid(ctx.ptr, kset.ptr, _ptr(image), _ptr(grid), _stream(stream)), "aw_image_to_grid")
+
+
+def aw_degrid_subtract(ctx: Handle, plan: Handle, kset: Handle, grid, vis, vis_out, stream=None):
+    _check(load().aw_degrid_subtract(ctx.ptr, plan.ptr, kset.ptr, _ptr(grid), _ptr(vis), _ptr(vis_out),
+                                     _stream(stream)), "aw_degrid_subtract")
+
+
+def aw_psf_sidelobe(ctx: Handle, psf, stream=None) -> float:
+    out = ctypes.c_float(0.0)
+    _check(load().aw_psf_sidelobe(ctx.ptr, _ptr(psf), int(psf.shape[-1]), ctypes.byref(out), _stream(stream)),
+           "aw_psf_sidelobe")
+    return out.value
+
+
+def aw_hogbom(ctx: Handle, residual, psf, gain: float, threshold: float, max_iter: int, patch_half: int,
+              window, model, stream=None) -> int:
+    """residual, model: CUDA float [npol][N][N] (updated); psf: CUDA float [N][N]."""
+    npol, N = int(residual.shape[0]), int(residual.shape[-1])
+    win = (c_i32 * 4)(*[int(x) for x in window])
+    n = c_i32(0)
+    _check(load().aw_hogbom(ctx.ptr, _ptr(residual), _ptr(psf), npol, N, ctypes.c_float(gain),
+                            ctypes.c_float(threshold), int(max_iter), int(patch_half), win, _ptr(model),
+                            ctypes.byref(n), _stream(stream)), "aw_hogbom")
+    return n.value
+
+
+def aw_clean(ctx: Handle, plan: Handle, kgrid: Handle, kdegrid: Handle, vis, weight, model, residual, psf,
+             n_major: int, max_minor: int, gain: float, threshold: float, cycle_factor: float, patch_half: int,
+             window=(0, 0, 0, 0), stream=None) -> aw_clean_report:
+    cfg = aw_clean_cfg(n_major, max_minor, gain, threshold, cycle_factor, patch_half,
+                       (c_i32 * 4)(*[int(x) for x in window]))
+    rep = aw_clean_report()
+    _check(load().aw_clean(ctx.ptr, plan.ptr, kgrid.ptr, kdegrid.ptr, _ptr(vis), _ptr(weight), ctypes.byref(cfg),
+                           _ptr(model), _ptr(residual), _ptr(psf), ctypes.byref(rep), _stream(stream)), "aw_clean")
+    return rep
 
 
 def device_observation(ob, device="cuda:0", flags=None):

@@ -412,6 +412,7 @@ struct DegridArgs {
     const int32_t *bin_support;
     const float2 *grid;
     float2 *vis_out;
+    const float2 *sub_from;  // if set: vis_out = sub_from - prediction (may alias vis_out)
     int N, OS;
     float inv_scale;
 };
@@ -649,6 +650,13 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
                         for (int c = 0; c < NPOL; ++c) out[c].y = -out[c].y;
                         if (NPOL == 4) { float2 t = out[1]; out[1] = out[2]; out[2] = t; }
                     }
+                    if (a.sub_from) {
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c) {
+                            const float2 o = a.sub_from[(int64_t)r.orig * NPOL + c];
+                            out[c] = make_float2(o.x - out[c].x, o.y - out[c].y);
+                        }
+                    }
                     float2 *dst = a.vis_out + (int64_t)r.orig * NPOL;
                     if constexpr (NPOL == 4) {
                         reinterpret_cast<float4 *>(dst)[0] = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
@@ -669,9 +677,9 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
     // visibilities that were not gridded (outside or flagged) predict zero
     for (int64_t i = a.nvalid + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.nvis;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float2 *dst = a.vis_out + (int64_t)a.rec[i].orig * NPOL;
+        const int64_t o = (int64_t)a.rec[i].orig * NPOL;
 #pragma unroll
-        for (int c = 0; c < NPOL; ++c) dst[c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < NPOL; ++c) a.vis_out[o + c] = a.sub_from ? a.sub_from[o + c] : make_float2(0.f, 0.f);
     }
 }
 
@@ -794,9 +802,10 @@ int aw_launch_grid(const aw_grid_launch &L) {
 }
 
 int aw_launch_degrid(const aw_plan *p, const aw_kernel_set *k, const void *grid, void *vis_out,
-                     cudaStream_t s) {
+                     cudaStream_t s, const void *sub_from) {
     if (p->nvis == 0) return AW_OK;
     DegridArgs a;
+    a.sub_from = reinterpret_cast<const float2 *>(sub_from);
     a.rec = p->d_rec;
     a.rec_dg = p->d_rec_dg;
     a.items = p->d_items_dg;

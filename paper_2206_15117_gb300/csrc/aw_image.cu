@@ -35,6 +35,22 @@ __global__ void gridcorr_kernel(const float2 *Z, const float *corr, int N, int64
     }
 }
 
+// grid = (-1)^(qx+qy) I(q) / (c[qx] c[qy]) as complex, zero on row/col 0 (the
+// first half of the model-image -> grid step; a forward FFT and the checker follow)
+__global__ void image_prep_kernel(const float *img, const float *corr, int N, int64_t total, float2 *g) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pix = i % ((int64_t)N * N);
+        const int y = (int)(pix / N), x = (int)(pix % N);
+        float v = 0.f;
+        if (x != 0 && y != 0) {
+            v = img[i] / (corr[x] * corr[y]);
+            if ((x + y) & 1) v = -v;
+        }
+        g[i] = make_float2(v, 0.f);
+    }
+}
+
 __global__ void gamma_max_kernel(const float *B, int nfield, int64_t npix, unsigned int *maxbits) {
     float m = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix;
@@ -108,6 +124,30 @@ int aw_fft_to_image_impl(aw_ctx *ctx, int N, int npol, double W, void *grid, dou
     AW_CUFFT_TRY(cufftExecC2C(plan, reinterpret_cast<cufftComplex *>(g), reinterpret_cast<cufftComplex *>(g),
                               CUFFT_INVERSE));
     gridcorr_kernel<<<nblocks(total, 256), 256, 0, s>>>(g, corr, N, total, (float)(1.0 / weight_sum), image);
+    AW_CHECK_LAUNCH();
+    return AW_OK;
+}
+
+// G(g) = sum_q I(q) / c(q) exp(-2 pi i (g - N/2)(q - N/2) / N): with N a multiple
+// of 4 the centring phases reduce to (-1)^(q) before and (-1)^(g) after a plain
+// forward FFT.
+int aw_image_to_grid_impl(aw_ctx *ctx, int N, int npol, double W, const float *image, void *grid,
+                          cudaStream_t s) {
+    if (N % 4) return aw_set_error(AW_EINVAL, "N must be a multiple of 4");
+    float *corr = nullptr;
+    int rc = aw_ctx_gridcorr(ctx, N, W, &corr);
+    if (rc) return rc;
+    cufftHandle plan;
+    rc = aw_ctx_fft_plan(ctx, 2, N, npol, CUFFT_C2C, &plan);
+    if (rc) return rc;
+    AW_CUFFT_TRY(cufftSetStream(plan, s));
+    const int64_t total = (int64_t)npol * N * N;
+    float2 *g = reinterpret_cast<float2 *>(grid);
+    image_prep_kernel<<<nblocks(total, 256), 256, 0, s>>>(image, corr, N, total, g);
+    AW_CHECK_LAUNCH();
+    AW_CUFFT_TRY(cufftExecC2C(plan, reinterpret_cast<cufftComplex *>(g), reinterpret_cast<cufftComplex *>(g),
+                              CUFFT_FORWARD));
+    checker_kernel<<<nblocks(total, 256), 256, 0, s>>>(g, N, total);
     AW_CHECK_LAUNCH();
     return AW_OK;
 }

@@ -160,7 +160,11 @@ struct aw_grid_launch {
 };
 int aw_launch_grid(const aw_grid_launch &L);
 int aw_launch_degrid(const aw_plan *plan, const aw_kernel_set *kset, const void *grid,
-                     void *vis_out, cudaStream_t stream);
+                     void *vis_out, cudaStream_t stream, const void *sub_from = nullptr);
+int aw_fft_to_image_impl(aw_ctx *ctx, int N, int npol, double W, void *grid, double weight_sum,
+                         float *image, cudaStream_t s);
+int aw_image_to_grid_impl(aw_ctx *ctx, int N, int npol, double W, const float *image, void *grid,
+                          cudaStream_t s);
 
 // Storage conversion (aw_synth.cu).
 int aw_export_table(const void *src, float2 *dst, int64_t nblocks, int L, int P, int ce, int storage,

@@ -90,7 +90,9 @@ def test_psf_sidelobe_of_a_hand_built_psf():
     psf[c, c + 3] = -0.5        # first non-positive value along +l: main-lobe radius 3
     psf[c + 3, c] = -0.45       # radius 3: inside the main lobe (not > 3)
     psf[c - 4, c + 2] = 0.25    # radius sqrt(20) > 3
-    psf[c + 5, c - 5] = -0.3    # the largest |psf| outside the main lobe
+    psf[c + 5, c - 5] = -0.3    # the largest |psf| outside the main lobe within N/4
+    psf[c + 8, c] = 0.9         # |dy| = N/4: beyond the sidelobe region
+    psf[c - 2, c - 9] = -0.8    # |dx| > N/4
     assert ocl.psf_sidelobe(psf) == np.float32(0.3)
 
 
