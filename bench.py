@@ -55,6 +55,8 @@ def parse():
                          "32 w-plane kernels (same per-bin density and tables, 1/32 of the memory)")
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
+    ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
+    ap.add_argument("--clean-major", type=int, default=3, help="major cycles of the cleaning measurement")
     ap.add_argument("--learned-steps", type=int, default=8000)
     ap.add_argument("--learned-fraction", type=float, default=0.1,
                     help="fraction of the mosaic field's visibilities gridded by both kernel paths")
@@ -228,6 +230,80 @@ def workload_config(ob, kw, info):
 
 
 # ----------------------------------------------------------------------------- learned surrogate
+def clean_section(ctx, dev, args, ob, kw, plan, kg, kd, stream):
+    """Cotton-Schwab cleaning (aw_clean) on the bench workload.  The observed
+    visibilities are the library's own prediction of the generator's point
+    sources (Stokes I, Q, U, V = 1, 0.05, -0.03, 0.005 of the flux), so the
+    loop must converge to them; timed with CUDA events.  The Hogbom minor
+    cycle is also timed alone, beside the oracle's FP32 minor cycle on the
+    same image."""
+    import torch
+    from oracle import clean as ocl
+    from paper_2206_15117_gb300 import aw
+    N = kw["N"]
+    dl = kw["dl"]
+    src = np.asarray(ob.sources)
+    qx = np.clip(np.rint(src[:, 0] / dl).astype(int) + N // 2, N // 4, 3 * N // 4 - 1)
+    qy = np.clip(np.rint(src[:, 1] / dl).astype(int) + N // 2, N // 4, 3 * N // 4 - 1)
+    truth = np.zeros((4, N, N), np.float32)
+    for k in range(len(src)):
+        truth[:, qy[k], qx[k]] += np.float32(src[k, 2]) * np.array([1.0, 0.05, -0.03, 0.005], np.float32)
+    t_dev = torch.as_tensor(truth, device=dev)
+    g = torch.empty((4, N, N), dtype=torch.complex64, device=dev)
+    aw.aw_image_to_grid(ctx, kd, t_dev, g)
+    vis_obs = torch.empty((ob.nvis, 4), dtype=torch.complex64, device=dev)
+    aw.aw_degrid(ctx, plan, kd, g, vis_obs)
+    del g
+    model = torch.empty((4, N, N), dtype=torch.float32, device=dev)
+    resid = torch.empty_like(model)
+    psf = torch.empty((N, N), dtype=torch.float32, device=dev)
+    cfg = dict(n_major=args.clean_major, max_minor=2000, gain=0.1, threshold=0.002, cycle_factor=1.5,
+               patch_half=256)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rep = aw.aw_clean(ctx, plan, kg, kd, vis_obs, None, model, resid, psf, **cfg)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clean_ms = a.elapsed_time(b)
+    m = model[0].cpu().numpy()
+    flux_true = float(truth[0].sum())
+    flux_at_src = float(sum(m[qy[k], qx[k]] for k in set(range(len(src)))))
+    # the minor cycle alone, on the dirty image of the observation
+    gd = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
+    aw.aw_grid_batched(ctx, plan, kg, vis_obs, None, gd)
+    dirty = torch.empty((4, N, N), dtype=torch.float32, device=dev)
+    aw.aw_fft_to_image(ctx, kg, gd, float(rep.weight_sum), dirty)
+    del gd
+    dirty_host = dirty.cpu().numpy()
+    psf_host = psf.cpu().numpy()
+    win = ocl.default_window(N)
+    m2 = torch.zeros_like(model)
+    n_it = 1000
+    torch.cuda.synchronize()
+    a.record(stream)
+    n_done = aw.aw_hogbom(ctx, dirty, psf, 0.1, 0.0, n_it, 256, win, m2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    hog_ms = a.elapsed_time(b)
+    n_cpu = 20
+    t0 = time.perf_counter()
+    _, _, n_cpu_done = ocl.hogbom(dirty_host, psf_host, 0.1, 0.0, n_cpu, 256, win)
+    cpu_s = time.perf_counter() - t0
+    del vis_obs, model, resid, psf, dirty, m2
+    torch.cuda.empty_cache()
+    return {"workload": "the bench workload (%d visibilities, 4096^2 x 4) predicted from the generator's "
+                        "%d point sources; gain 0.1, cycle factor 1.5, PSF patch 513^2, threshold 2 mJy"
+                        % (ob.nvis, len(src)),
+            "ms_total": clean_ms, "n_major": rep.n_major, "n_minor": rep.n_minor,
+            "ms_per_major_cycle": clean_ms / max(rep.n_major + 2, 1),
+            "peak_first": rep.peak_first, "peak_last": rep.peak_last, "psf_sidelobe": rep.sidelobe,
+            "stokes_i_flux_true": flux_true, "stokes_i_flux_on_source_pixels": flux_at_src,
+            "hogbom_iterations_per_s": n_done / (hog_ms / 1e3), "hogbom_iterations": n_done,
+            "oracle_hogbom_iterations_per_s": n_cpu_done / cpu_s,
+            "note": "ms_per_major_cycle counts the PSF and final residual passes as cycles"}
+
+
 def learned_section(ctx, dev, args):
     """The learned AW-kernel surrogate on the mosaic workload: 4 x 128 SIREN
     trained on the exact full-pol kernels of the configuration-2 bins (32 w
@@ -544,6 +620,9 @@ def run_ours(args, rank, world, dist):
                "d2h_bytes_per_step": int(nbytes), "ms_per_step": e_ms,
                "how": "pinned host visibilities copied in, grid + FFT + degrid, predicted visibilities copied out"}
 
+    clean = None
+    if not args.no_clean and not args.subset:
+        clean = clean_section(ctx, dev, args, ob, kw, plan, kg, kd, stream)
     learned = None
     if not args.no_learned:
         # free the FP32 workload before the learned comparison
@@ -573,7 +652,7 @@ def run_ours(args, rank, world, dist):
                 "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm,
                          "dg_tile": tune.dg_tile or 1024, "degrid_items": info.nitems_degrid,
                          "grid_schedule": ["tiles", "offsets"][tune.grid_mode]},
-                "learned": learned}
+                "clean": clean, "learned": learned}
         print(json.dumps(line), flush=True)
     return 0
 

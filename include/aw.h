@@ -511,9 +511,11 @@ int aw_psf_sidelobe(aw_ctx *ctx, const float *psf, int32_t N, float *sidelobe, v
  * device float [npol][N][N], updated in place; psf: device float [N][N] with
  * its peak at (N/2, N/2); model: device float [npol][N][N], components added;
  * window: host int32[4] (x0, y0, x1, y1, half-open, non-empty, inside the
- * image).  One CTA runs the loop; the peak search keeps the maximum of each
+ * image).  One cooperative grid (one or two blocks per SM) runs the loop with
+ * three grid barriers per iteration; the peak search keeps the maximum of each
  * 64 x 64 tile (or larger, at most 64 x 64 tiles) and rescans only the tiles a
- * subtraction touched.  *n_iter: host.  Synchronises `stream`.
+ * subtraction touched.  Barrier waits are bounded: AW_ETIMEOUT if one gives
+ * up (results invalid).  *n_iter: host.  Synchronises `stream`.
  */
 int aw_hogbom(aw_ctx *ctx, float *residual, const float *psf, int32_t npol, int32_t N, float gain,
               float threshold, int32_t max_iter, int32_t patch_half, const int32_t *window, float *model,

@@ -37,6 +37,11 @@ constexpr int SCR_R0 = 4;        // main-lobe radius
 constexpr int SCR_SIDE = 5;      // sidelobe level (float bits, >= 0)
 constexpr int SCR_PEAK = 6;      // window peak |I| (float bits, >= 0)
 constexpr int SCR_NITER = 7;     // Hogbom iterations
+constexpr int SCR_BAR_COUNT = 8; // grid barrier: arrivals
+constexpr int SCR_BAR_GEN = 9;   // grid barrier: generation
+constexpr int SCR_BAR_ERR = 10;  // grid barrier: set when a wait gave up
+// spin limit of one barrier wait: 2^24 polls of >= 64 ns, about a second or more
+constexpr long long BAR_SPIN_LIMIT = 1ll << 24;
 
 // ---------------------------------------------------------------- sidelobe
 // r0 = first x > 0 with psf[c][c + x] <= 0 (N/2 if none), one warp.
@@ -134,76 +139,136 @@ __global__ void hb_tiles_kernel(const float *R0, HbGeom g, unsigned long long *t
     if (threadIdx.x == 0) tmax[blockIdx.x] = v;
 }
 
-constexpr int HB_THREADS = 1024;
+constexpr int HB_THREADS = 256;
 
-// The minor cycle in one CTA.  Per iteration: the maximum over the tile
-// maxima picks the pixel; thread 0 forms the component (gain x residual, all
-// planes) and adds it to the model; the block subtracts component x psf over
-// the patch (FP32, one rounding per multiply and per subtraction); the tiles
-// the patch touched are rescanned.
+// Barrier over all blocks of a cooperative launch (co-residency guaranteed by
+// the launch).  The last block to arrive resets the count and advances the
+// generation; the others poll the generation with a bounded wait.  A wait that
+// runs out sets the error word and returns false, so that no block can wait
+// for ever; the caller then leaves its loop.
+__device__ bool grid_barrier(unsigned int *scr, unsigned int nblocks, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = scr + SCR_BAR_GEN;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(scr + SCR_BAR_COUNT, 1u) + 1u;
+        int ok = 1;
+        if (arrived == nblocks) {
+            atomicExch(scr + SCR_BAR_COUNT, 0u);
+            __threadfence();
+            atomicAdd(scr + SCR_BAR_GEN, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g0) {
+                if (++spins > BAR_SPIN_LIMIT || *(volatile unsigned int *)(scr + SCR_BAR_ERR)) {
+                    atomicExch(scr + SCR_BAR_ERR, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Maximum of tile t over its window pixels, by one block, reading the
+// residual through L2 (other blocks write it between grid barriers).
+__device__ unsigned long long tile_scan_l2(const float *R0, const HbGeom &g, int t, unsigned long long *red) {
+    const int tx = t % g.TX, ty = t / g.TX;
+    const int xa = max(tx * g.T, g.x0), xb = min((tx + 1) * g.T, g.x1);
+    const int ya = max(ty * g.T, g.y0), yb = min((ty + 1) * g.T, g.y1);
+    unsigned long long v = 0ull;
+    if (xa < xb && ya < yb) {
+        const int w = xb - xa, cnt = w * (yb - ya);
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const uint32_t idx = (uint32_t)(ya + e / w) * (uint32_t)g.N + (uint32_t)(xa + e % w);
+            const unsigned long long p = hb_pack(__ldcg(R0 + idx), idx);
+            v = p > v ? p : v;
+        }
+    }
+    return block_max_u64(v, red);
+}
+
+// The minor cycle as one cooperative grid.  Per iteration: every block finds
+// the same peak from the tile maxima (global, read through L2) and the same
+// component (gain x residual, all planes); after a grid barrier block 0 adds
+// the component to the model and all blocks subtract component x psf over the
+// patch (FP32, one rounding per multiply and per subtraction); after a second
+// barrier the blocks rescan the touched tiles; a third barrier ends the
+// iteration.  Every block takes the same stop decision from the same data.
 __global__ void __launch_bounds__(HB_THREADS) hogbom_kernel(float *R, const float *psf, float *model, int npol,
                                                             HbGeom g, float gain, float thr, int max_iter,
-                                                            int h, const unsigned long long *tmax_in,
-                                                            unsigned int *scr) {
-    extern __shared__ unsigned long long tmax[];
+                                                            int h, unsigned long long *tmax, unsigned int *scr) {
+    __shared__ int s_ok;
     __shared__ unsigned long long red[33];
     __shared__ float comp[4];
     __shared__ int s_stop, s_py, s_px;
+    __shared__ uint32_t s_idx;
     const int ntiles = g.TX * g.TX;
     const int64_t NN = (int64_t)g.N * g.N;
     const int c = g.N / 2;
-    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) tmax[i] = tmax_in[i];
-    __syncthreads();
-    int n = 0;
-    for (;;) {
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int n = 0;; ++n) {
         unsigned long long v = 0ull;
-        for (int i = threadIdx.x; i < ntiles; i += blockDim.x) v = tmax[i] > v ? tmax[i] : v;
+        for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+            const unsigned long long t = __ldcg(tmax + i);
+            v = t > v ? t : v;
+        }
         const unsigned long long best = block_max_u64(v, red);
         if (threadIdx.x == 0) {
             int stop = (best == 0ull || n >= max_iter) ? 1 : 0;
             if (!stop) {
                 const uint32_t idx = 0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFull);
-                if (fabsf(R[idx]) < thr) {
+                if (fabsf(__ldcg(R + idx)) < thr) {
                     stop = 1;
                 } else {
-                    for (int s = 0; s < npol; ++s) {
-                        const float cs = __fmul_rn(gain, R[s * NN + idx]);
-                        comp[s] = cs;
-                        model[s * NN + idx] = __fadd_rn(model[s * NN + idx], cs);
-                    }
+                    for (int s = 0; s < npol; ++s) comp[s] = __fmul_rn(gain, __ldcg(R + s * NN + idx));
+                    s_idx = idx;
                     s_py = (int)(idx / (uint32_t)g.N);
                     s_px = (int)(idx % (uint32_t)g.N);
                 }
             }
             s_stop = stop;
+            if (stop && blockIdx.x == 0) scr[SCR_NITER] = (unsigned)n;
         }
         __syncthreads();
         if (s_stop) break;
+        if (!grid_barrier(scr, gridDim.x, &s_ok)) break;  // every block has read the residual at the peak
+        if (blockIdx.x == 0 && threadIdx.x < npol) {
+            const int64_t o = threadIdx.x * NN + s_idx;
+            model[o] = __fadd_rn(model[o], comp[threadIdx.x]);
+        }
         const int py = s_py, px = s_px;
         const int ya = max(0, py - h), yb = min(g.N, py + h + 1);
         const int xa = max(0, px - h), xb = min(g.N, px + h + 1);
-        const int w = xb - xa, cnt = w * (yb - ya);
-        for (int e = threadIdx.x; e < npol * cnt; e += blockDim.x) {
-            const int s = e / cnt, r = e - s * cnt;
-            const int y = ya + r / w, x = xa + r % w;
+        const int w = xb - xa;
+        const int64_t cnt = (int64_t)w * (yb - ya);
+        for (int64_t e = gtid; e < npol * cnt; e += gthreads) {
+            const int s = (int)(e / cnt);
+            const int64_t r = e - s * cnt;
+            const int y = ya + (int)(r / w), x = xa + (int)(r % w);
             float *p = R + s * NN + (int64_t)y * g.N + x;
-            *p = __fsub_rn(*p, __fmul_rn(comp[s], psf[(int64_t)(c + y - py) * g.N + (c + x - px)]));
+            *p = __fsub_rn(__ldcg(p), __fmul_rn(comp[s], psf[(int64_t)(c + y - py) * g.N + (c + x - px)]));
         }
-        __syncthreads();
-        // rescan the tiles of the patch that meet the window
+        if (!grid_barrier(scr, gridDim.x, &s_ok)) break;  // the patch is subtracted everywhere
         const int rxa = max(xa, g.x0), rxb = min(xb, g.x1), rya = max(ya, g.y0), ryb = min(yb, g.y1);
         if (rxa < rxb && rya < ryb) {
-            for (int ty = rya / g.T; ty <= (ryb - 1) / g.T; ++ty)
-                for (int tx = rxa / g.T; tx <= (rxb - 1) / g.T; ++tx) {
-                    const int t = ty * g.TX + tx;
-                    const unsigned long long tv = tile_scan(R, g, t, red);
-                    if (threadIdx.x == 0) tmax[t] = tv;
-                }
+            const int tx0 = rxa / g.T, tx1 = (rxb - 1) / g.T, ty0 = rya / g.T, ty1 = (ryb - 1) / g.T;
+            const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+            for (int k = blockIdx.x; k < nt; k += gridDim.x) {
+                const int t = (ty0 + k / ntx) * g.TX + tx0 + k % ntx;
+                const unsigned long long tv = tile_scan_l2(R, g, t, red);
+                if (threadIdx.x == 0) tmax[t] = tv;
+            }
         }
-        __syncthreads();
-        ++n;
+        if (!grid_barrier(scr, gridDim.x, &s_ok)) break;  // the tile maxima are current
     }
-    if (threadIdx.x == 0) scr[SCR_NITER] = (unsigned)n;
 }
 
 // ---------------------------------------------------------------- clean helpers
@@ -244,25 +309,29 @@ HbGeom geom_of(int N, const int32_t *win) {
 
 int hogbom_impl(aw_ctx *ctx, float *R, const float *psf, int npol, int N, float gain, float thr, int max_iter,
                 int h, const int32_t *win, float *model, int32_t *n_iter, cudaStream_t s) {
-    const HbGeom g = geom_of(N, win);
+    HbGeom g = geom_of(N, win);
     const int ntiles = g.TX * g.TX;
     unsigned long long *tmax = nullptr;
     AW_CUDA_TRY(cudaMallocAsync(&tmax, sizeof(unsigned long long) * ntiles, s));
     hb_tiles_kernel<<<ntiles, 256, 0, s>>>(R, g, tmax);
     cudaError_t e = cudaGetLastError();
-    const size_t smem = sizeof(unsigned long long) * ntiles;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(hogbom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // one co-resident block per SM (at most 2): the barriers cost more than the work
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hogbom_kernel, HB_THREADS, 0);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorCooperativeLaunchTooLarge;
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_scratch + SCR_BAR_COUNT, 0, 3 * sizeof(unsigned int), s);
     if (e == cudaSuccess) {
-        hogbom_kernel<<<1, HB_THREADS, smem, s>>>(R, psf, model, npol, g, gain, thr, max_iter, h, tmax,
-                                                  ctx->d_scratch);
-        e = cudaGetLastError();
+        const int blocks = ctx->sm_count * std::min(per_sm, 2);
+        void *args[] = {&R, (void *)&psf, &model, &npol, &g, &gain, &thr, &max_iter, &h, &tmax, &ctx->d_scratch};
+        e = cudaLaunchCooperativeKernel((const void *)hogbom_kernel, dim3(blocks), dim3(HB_THREADS), args, 0, s);
     }
     cudaFreeAsync(tmax, s);
     if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "hogbom: %s", cudaGetErrorString(e));
-    unsigned int n = 0;
-    AW_CUDA_TRY(cudaMemcpyAsync(&n, ctx->d_scratch + SCR_NITER, sizeof(n), cudaMemcpyDeviceToHost, s));
+    unsigned int w[4] = {0, 0, 0, 0};  // iterations, barrier count, generation, error
+    AW_CUDA_TRY(cudaMemcpyAsync(w, ctx->d_scratch + SCR_NITER, sizeof(w), cudaMemcpyDeviceToHost, s));
     AW_CUDA_TRY(cudaStreamSynchronize(s));
-    *n_iter = (int32_t)n;
+    if (w[3]) return aw_set_error(AW_ETIMEOUT, "hogbom: a grid barrier wait gave up; results are invalid");
+    *n_iter = (int32_t)w[0];
     return AW_OK;
 }
 

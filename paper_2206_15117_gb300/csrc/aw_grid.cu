@@ -504,7 +504,7 @@ __device__ __forceinline__ void smem_krow(const char *slab, int tl, int c, float
 // visibility first, then apply the kernel one Mueller row at a time.  Partial
 // sums (AW_DG_VB x NPOL complex per lane) are reduce-scattered over the warp
 // and summed across the group's warps in shared memory.
-template <int NPOL, int ST>
+template <int NPOL, int ST, bool SUB>
 __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
     constexpr int P = NPOL * NPOL;
     constexpr int VB = AW_DG_VB;
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
                         for (int c = 0; c < NPOL; ++c) out[c].y = -out[c].y;
                         if (NPOL == 4) { float2 t = out[1]; out[1] = out[2]; out[2] = t; }
                     }
-                    if (a.sub_from) {
+                    if constexpr (SUB) {
 #pragma unroll
                         for (int c = 0; c < NPOL; ++c) {
                             const float2 o = a.sub_from[(int64_t)r.orig * NPOL + c];
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (int64_t)a.rec[i].orig * NPOL;
 #pragma unroll
-        for (int c = 0; c < NPOL; ++c) a.vis_out[o + c] = a.sub_from ? a.sub_from[o + c] : make_float2(0.f, 0.f);
+        for (int c = 0; c < NPOL; ++c) a.vis_out[o + c] = SUB ? a.sub_from[o + c] : make_float2(0.f, 0.f);
     }
 }
 
@@ -702,20 +702,25 @@ int launch_grid_t(const aw_grid_launch &L, const GridArgs &a) {
     return AW_OK;
 }
 
-template <int NPOL, int ST>
-int launch_degrid_t(const DegridArgs &a, int sm_count, cudaStream_t s) {
+template <int NPOL, int ST, bool SUB>
+int launch_degrid_ts(const DegridArgs &a, int sm_count, cudaStream_t s) {
     const size_t smem = degrid_smem_bytes<NPOL, ST>();
-    AW_CUDA_TRY(cudaFuncSetAttribute(degrid_items_kernel<NPOL, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    AW_CUDA_TRY(cudaFuncSetAttribute(degrid_items_kernel<NPOL, ST, SUB>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;
-    AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degrid_items_kernel<NPOL, ST>, 256, smem));
+    AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degrid_items_kernel<NPOL, ST, SUB>, 256, smem));
     int64_t blocks = a.nitems;
     const int64_t cap = (int64_t)sm_count * std::max(per_sm, 1);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    degrid_items_kernel<NPOL, ST><<<(unsigned)blocks, 256, smem, s>>>(a);
+    degrid_items_kernel<NPOL, ST, SUB><<<(unsigned)blocks, 256, smem, s>>>(a);
     AW_CHECK_LAUNCH();
     return AW_OK;
+}
+
+template <int NPOL, int ST>
+int launch_degrid_t(const DegridArgs &a, int sm_count, cudaStream_t s) {
+    return a.sub_from ? launch_degrid_ts<NPOL, ST, true>(a, sm_count, s) : launch_degrid_ts<NPOL, ST, false>(a, sm_count, s);
 }
 
 
