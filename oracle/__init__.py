@@ -15,6 +15,7 @@ core  : the method in plain NumPy/FP64 (prolate-spheroidal taper, Jones and
         direct DFT).
 mlp   : FP64 SIREN surrogate forward, analytic backward and Adam step.
 clean : Cotton-Schwab major cycles around an FP32 Hogbom minor cycle.
+mosaic: image-plane reprojection between SIN frames and the Eq. 1 combination.
 
 Parity status: every function is pinned by tests under ``tests/`` against
 values the paper prints, closed forms, library special functions or brute
