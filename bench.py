@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
+    ap.add_argument("--no-mosaic", action="store_true", help="skip the image-domain mosaic measurement")
     ap.add_argument("--clean-major", type=int, default=3, help="major cycles of the cleaning measurement")
     ap.add_argument("--learned-steps", type=int, default=8000)
     ap.add_argument("--learned-fraction", type=float, default=0.1,
@@ -302,6 +303,76 @@ def clean_section(ctx, dev, args, ob, kw, plan, kg, kd, stream):
             "hogbom_iterations_per_s": n_done / (hog_ms / 1e3), "hogbom_iterations": n_done,
             "oracle_hogbom_iterations_per_s": n_cpu_done / cpu_s,
             "note": "ms_per_major_cycle counts the PSF and final residual passes as cycles"}
+
+
+def mosaic_section(ctx, dev, args, stream):
+    """Image-domain mosaic round trip (Sec. 2.2) at the mosaic geometry of the
+    learned-kernel workload: 7 hexagonal fields 1 deg apart at dec -45 deg,
+    2048^2 x 4 Stokes planes over 3 deg each, into a 4096^2 common frame at the
+    same pixel size; Airy power beams of a 12 m dish at 1.35 GHz.  Timed: the 7
+    reprojections to the common frame (Keys cubic) and the Eq. 1 combination;
+    then the 7 reprojections of the model back to the fields."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import synthetic as sy
+    Nf, Nm = 2048, 4096
+    dl = math.radians(3.0) / Nf
+    dec0 = math.radians(-45.0)
+    ra0 = 1.0
+    fields = []
+    for (ex_deg, no_deg) in sy.mosaic_offsets():
+        fields.append(aw.sky_frame(ra0 + math.radians(ex_deg) / math.cos(dec0), dec0 + math.radians(no_deg), dl, Nf))
+    mframe = aw.sky_frame(ra0, dec0, dl, Nm)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(77)
+    imgs = torch.randn((len(fields), 4, Nf, Nf), dtype=torch.float32, device=dev, generator=gen)
+    # Airy power beams of each pointing on the common frame (flat-sky offsets)
+    q = (torch.arange(Nm, device=dev, dtype=torch.float64) - Nm // 2) * dl
+    lam = 299792458.0 / 1.35e9
+    beams = torch.empty((len(fields), Nm, Nm), dtype=torch.float32, device=dev)
+    from scipy.special import j1
+    for f, (ex_deg, no_deg) in enumerate(sy.mosaic_offsets()):
+        r = torch.hypot(q[None, :] - math.radians(ex_deg), q[:, None] - math.radians(no_deg))
+        x = (math.pi * 12.0 / lam * r).cpu().numpy()
+        e = np.where(x == 0, 1.0, 2.0 * j1(np.where(x == 0, 1.0, x)) / np.where(x == 0, 1.0, x))
+        beams[f] = torch.as_tensor((e * e).astype(np.float32), device=dev)
+    gam = torch.empty((Nm, Nm), dtype=torch.float32, device=dev)
+    aw.mosaic_gamma(ctx, beams, 0.2, gam)
+    onm = torch.empty((len(fields), 4, Nm, Nm), dtype=torch.float32, device=dev)
+    mosaic = torch.empty((4, Nm, Nm), dtype=torch.float32, device=dev)
+    back = torch.empty_like(imgs)
+
+    def forward():
+        for f, fr in enumerate(fields):
+            aw.aw_reproject(ctx, imgs[f], fr, onm[f], mframe, aw.AW_INTERP_CUBIC)
+        aw.aw_mosaic_combine(ctx, onm, beams, gam, mosaic)
+
+    def backward():
+        for f, fr in enumerate(fields):
+            aw.aw_reproject(ctx, mosaic, mframe, back[f], fr, aw.AW_INTERP_CUBIC)
+
+    res = {}
+    for name, fn in (("forward", forward), ("backward", backward)):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / reps
+    out_px_fwd = len(fields) * Nm * Nm
+    out_px_bwd = len(fields) * Nf * Nf
+    del imgs, beams, gam, onm, mosaic, back
+    torch.cuda.empty_cache()
+    return {"workload": "7 fields of 2048^2 x 4 (3 deg, hexagonal 1 deg apart, dec -45) <-> 4096^2 x 4 common frame, "
+                        "Keys cubic",
+            "ms_fields_to_mosaic_and_combine": res["forward"], "ms_mosaic_to_fields": res["backward"],
+            "gpix_per_s_fields_to_mosaic": out_px_fwd / (res["forward"] / 1e3) / 1e9,
+            "gpix_per_s_mosaic_to_fields": out_px_bwd / (res["backward"] / 1e3) / 1e9,
+            "note": "a pixel = all 4 Stokes planes; FP64 position (3x3 rotation) and floor, FP32 weights and 4x4 interpolation"}
 
 
 def learned_section(ctx, dev, args):
@@ -623,6 +694,9 @@ def run_ours(args, rank, world, dist):
     clean = None
     if not args.no_clean and not args.subset:
         clean = clean_section(ctx, dev, args, ob, kw, plan, kg, kd, stream)
+    mosaic = None
+    if not args.no_mosaic and not args.subset:
+        mosaic = mosaic_section(ctx, dev, args, stream)
     learned = None
     if not args.no_learned:
         # free the FP32 workload before the learned comparison
@@ -652,7 +726,7 @@ def run_ours(args, rank, world, dist):
                 "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm,
                          "dg_tile": tune.dg_tile or 1024, "degrid_items": info.nitems_degrid,
                          "grid_schedule": ["tiles", "offsets"][tune.grid_mode]},
-                "clean": clean, "learned": learned}
+                "clean": clean, "mosaic": mosaic, "learned": learned}
         print(json.dumps(line), flush=True)
     return 0
 

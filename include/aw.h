@@ -440,6 +440,48 @@ int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, flo
 int mosaic_gamma_noalloc(const float *beams, int32_t nfield, int32_t N, float eps, float *gamma,
                          void *stream);
 
+/* ---- image-domain mosaics: reprojection and combination ----------------------
+ *
+ * Sec. 2.2: each mosaic field is imaged at its own phase centre; image-plane
+ * reprojection brings the images to a common phase position to form the
+ * mosaic, and the model is reprojected back to each field before degridding.
+ * Readings: frames are orthographic (SIN) projections about a phase centre
+ * (ra0, dec0), with l = cos dec sin(ra - ra0), m = sin dec cos dec0 -
+ * cos dec sin dec0 cos(ra - ra0); pixel (qx, qy) of a frame sits at
+ * l = (qx - cx) dl, m = (qy - cy) dl.  An output pixel is carried to the
+ * source frame (FP64; the map between two frames is a rotation of
+ * (l, m, n)), and the source image is interpolated there: bilinear (2 x 2)
+ * or Keys cubic convolution, a = -1/2 (4 x 4), in FP32.  Where the stencil
+ * leaves the source image, or the direction is off the visible hemisphere of
+ * either frame, the output is `fill`.
+ */
+typedef struct aw_sky_frame {
+    double ra0, dec0;        /* phase centre, radians                              */
+    double dl;               /* pixel size, direction-cosine units (> 0)           */
+    double cx, cy;           /* pixel of the phase centre                          */
+    int32_t N;               /* image side (N x N pixels)                          */
+    int32_t reserved;
+} aw_sky_frame;
+
+enum { AW_INTERP_BILINEAR = 0, AW_INTERP_CUBIC = 1 };
+
+/*
+ * aw_reproject - src: device float [nplane][src->N][src->N]; dst: device
+ * float [nplane][dst->N][dst->N], overwritten; the planes share the pixel
+ * mapping.  Frames are host structs.
+ */
+int aw_reproject(aw_ctx *ctx, const float *src, const aw_sky_frame *src_frame, float *dst,
+                 const aw_sky_frame *dst_frame, int32_t nplane, int32_t interp, float fill, void *stream);
+
+/*
+ * aw_mosaic_combine - Eq. 1 on images already in the common frame:
+ * out[p] = gamma * sum_f beams[f] * images[f][p].  images: device float
+ * [nfield][nplane][N][N]; beams: device float [nfield][N][N]; gamma: device
+ * float [N][N] (mosaic_gamma); out: device float [nplane][N][N].
+ */
+int aw_mosaic_combine(aw_ctx *ctx, const float *images, const float *beams, const float *gamma, int32_t nfield,
+                      int32_t nplane, int32_t N, float *out, void *stream);
+
 /* ---- cleaning: Cotton-Schwab major cycles, Hogbom minor cycle ---------------
  *
  * Sec. 2.1: the imager cleans with the Cotton-Schwab algorithm, controlled by

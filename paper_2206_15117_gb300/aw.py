@@ -18,6 +18,7 @@ AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ETIMEOUT, AW_EUNSUPPORTED, AW_EREJECTE
 AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT = 0, 1, 2
 AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
 AW_GRID_TILES, AW_GRID_OFFSETS = 0, 1
+AW_INTERP_BILINEAR, AW_INTERP_CUBIC = 0, 1
 
 c_i32, c_i64, c_dbl, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -52,6 +53,18 @@ class aw_plan_info(ctypes.Structure):
     _fields_ = [("nvis", c_i64), ("nvalid", c_i64), ("n_outside", c_i64), ("n_flagged", c_i64),
                 ("nitems", c_i64), ("tile", c_i32), ("chunk", c_i32), ("mean_taps", c_dbl),
                 ("nitems_degrid", c_i64)]
+
+
+class aw_sky_frame(ctypes.Structure):
+    _fields_ = [("ra0", c_dbl), ("dec0", c_dbl), ("dl", c_dbl), ("cx", c_dbl), ("cy", c_dbl), ("N", c_i32),
+                ("reserved", c_i32)]
+
+
+def sky_frame(ra0: float, dec0: float, dl: float, N: int, cx: Optional[float] = None,
+              cy: Optional[float] = None) -> aw_sky_frame:
+    """SIN frame about (ra0, dec0); pixel (qx, qy) at l = (qx - cx) dl (cx, cy default N/2)."""
+    return aw_sky_frame(float(ra0), float(dec0), float(dl), float(N // 2 if cx is None else cx),
+                        float(N // 2 if cy is None else cy), int(N), 0)
 
 
 class aw_clean_cfg(ctypes.Structure):
@@ -94,6 +107,9 @@ SIGNATURES = {
     "mosaic_gamma": (ctypes.c_int, [c_p, c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
+    "aw_reproject": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(aw_sky_frame), c_p, ctypes.POINTER(aw_sky_frame),
+                                    c_i32, c_i32, ctypes.c_float, c_p]),
+    "aw_mosaic_combine": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_i32, c_i32, c_i32, c_p, c_p]),
     "aw_degrid_subtract": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_psf_sidelobe": (ctypes.c_int, [c_p, c_p, c_i32, ctypes.POINTER(ctypes.c_float), c_p]),
     "aw_hogbom": (ctypes.c_int, [c_p, c_p, c_p, c_i32, c_i32, ctypes.c_float, ctypes.c_float, c_i32, c_i32,
@@ -360,6 +376,21 @@ def mosaic_gamma_noalloc(beams, eps: float, gamma, stream=None):
 
 def aw_image_to_grid(ctx: Handle, kset: Handle, image, grid, stream=None):
     _check(load().aw_image_to_grid(ctx.ptr, kset.ptr, _ptr(image), _ptr(grid), _stream(stream)), "aw_image_to_grid")
+
+
+def aw_reproject(ctx: Handle, src, src_frame: aw_sky_frame, dst, dst_frame: aw_sky_frame,
+                 interp: int = AW_INTERP_CUBIC, fill: float = 0.0, stream=None):
+    """src: CUDA float [nplane][Ns][Ns] -> dst: CUDA float [nplane][Nd][Nd]."""
+    nplane = int(src.shape[0])
+    _check(load().aw_reproject(ctx.ptr, _ptr(src), ctypes.byref(src_frame), _ptr(dst), ctypes.byref(dst_frame),
+                               nplane, int(interp), ctypes.c_float(fill), _stream(stream)), "aw_reproject")
+
+
+def aw_mosaic_combine(ctx: Handle, images, beams, gamma, out, stream=None):
+    """images [nfield][nplane][N][N], beams [nfield][N][N], gamma [N][N] -> out [nplane][N][N]."""
+    nfield, nplane, N = int(images.shape[0]), int(images.shape[1]), int(images.shape[-1])
+    _check(load().aw_mosaic_combine(ctx.ptr, _ptr(images), _ptr(beams), _ptr(gamma), nfield, nplane, N, _ptr(out),
+                                    _stream(stream)), "aw_mosaic_combine")
 
 
 def aw_degrid_subtract(ctx: Handle, plan: Handle, kset: Handle, grid, vis, vis_out, stream=None):
