@@ -153,7 +153,9 @@ def oracle_sample(ob, kw, cpu_seconds: float, seed: int = 5):
     # every visibility of the picked bins: the rows/channels of their (PA, frequency)
     # bin pairs, then the oracle's own coordinates
     sel = []
-    budget_macs = cpu_seconds * 2.0e9     # grid + degrid cost ~ 2 x 16 S^2 complex MACs per visibility
+    # grid + degrid cost ~ 2 x 16 S^2 complex MACs per visibility; the FP64 C loops of the oracle
+    # run about 0.7e9 of them per second on one Grace core (measured)
+    budget_macs = cpu_seconds * 0.7e9
     for b in pick:
         a_, f_ = (b // spec.nfb) % spec.npa, b % spec.nfb
         cand = np.flatnonzero((ob.pa_bin[ob.row_of_vis] == a_) & (ob.fbin[ob.chan_of_vis] == f_))
@@ -200,7 +202,7 @@ def run_reference(args, rank, world):
     from oracle import build as ob_build
     ob_build.build()
     ob, kw = workload(args.time_samples, args.subset)
-    per_step = max(1.0, min(args.cpu_seconds, 180.0 / max(1, args.steps + args.warmup)))
+    per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     smp = oracle_sample(ob, kw, per_step)
     for _ in range(args.warmup):
         oracle_step(smp)
