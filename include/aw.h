@@ -392,8 +392,9 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exa
 /*
  * aw_grid_learned - gridding with the surrogate evaluated inline (no kernel
  * tables): for every visibility and tap of its footprint the MLP runs on
- * tensor cores (mma.sync, FP16 weights and activations, FP32 accumulation)
- * at the tap's exact offset from the visibility (no oversampling grid), the
+ * tensor cores (FP16 weights and activations, FP32 accumulation; engine
+ * chosen by aw_surrogate_set_engine) at the tap's exact offset from the
+ * visibility (no oversampling grid), the
  * visibility's exact |w| (no w-plane quantisation), its beam-frequency bin centre
  * and its parallactic-angle bin centre; the P kernel values are applied as
  * in aw_grid (same flip, weights, skip rules, accumulation into `grid`).
@@ -401,10 +402,23 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exa
  * planes rejected by the last aw_surrogate_tables call use `fallback` (the
  * exact set) at the plan's quantised offsets.  The surrogate must have width
  * 128 and 4 sine layers (AW_EUNSUPPORTED otherwise).  The plan's visibility
- * descriptor arrays are read again and must still be valid.
+ * descriptor arrays are read again and must still be valid.  With the
+ * TCGEN05 engine the call synchronises `stream` and returns AW_ETIMEOUT if a
+ * bounded tensor-core completion wait gave up (grid invalid).
  */
 int aw_grid_learned(aw_ctx *ctx, const aw_plan *plan, aw_surrogate *sur, const aw_kernel_set *fallback,
                     const void *vis, const float *weight, void *grid, aw_stats *stats, void *stream);
+
+/*
+ * aw_surrogate_set_engine - tensor-core generation of the inline evaluation in
+ * aw_grid_learned.  AW_ENGINE_TCGEN05 (default): 128-row tiles per CTA,
+ * tcgen05.mma with FP32 accumulators in tensor memory, one thread issuing.
+ * AW_ENGINE_MMA_SYNC: 16-row tiles per warp on mma.sync.m16n8k16.  Both give
+ * the same result up to FP32 summation order and the FP16 rounding of the
+ * activations.  AW_EINVAL for any other value.
+ */
+enum { AW_ENGINE_MMA_SYNC = 0, AW_ENGINE_TCGEN05 = 1 };
+int aw_surrogate_set_engine(aw_surrogate *sur, int32_t engine);
 
 /* ---- mosaic weighting (Sec. 2.2, Eq. 1) ------------------------------------- */
 

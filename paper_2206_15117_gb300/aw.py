@@ -19,6 +19,7 @@ AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT = 0, 1, 2
 AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
 AW_GRID_TILES, AW_GRID_OFFSETS = 0, 1
 AW_INTERP_BILINEAR, AW_INTERP_CUBIC = 0, 1
+AW_ENGINE_MMA_SYNC, AW_ENGINE_TCGEN05 = 0, 1
 
 c_i32, c_i64, c_dbl, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -107,6 +108,7 @@ SIGNATURES = {
     "mosaic_gamma": (ctypes.c_int, [c_p, c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
+    "aw_surrogate_set_engine": (ctypes.c_int, [c_p, c_i32]),
     "aw_reproject": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(aw_sky_frame), c_p, ctypes.POINTER(aw_sky_frame),
                                     c_i32, c_i32, ctypes.c_float, c_p]),
     "aw_mosaic_combine": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_i32, c_i32, c_i32, c_p, c_p]),
@@ -522,6 +524,10 @@ def aw_surrogate_tables(ctx: Handle, sur: Handle, exact: Handle, reject_rel: flo
         _check(rc, "aw_surrogate_tables")
     ks = Handle(out, "aw_kernel_set_destroy")
     return ks, err, aw_kernel_set_info(ks).n_rejected
+
+
+def aw_surrogate_set_engine(sur: Handle, engine: int):
+    _check(load().aw_surrogate_set_engine(sur.ptr, int(engine)), "aw_surrogate_set_engine")
 
 
 def aw_grid_learned(ctx: Handle, plan: Handle, sur: Handle, fallback: Handle, vis, weight, grid,

@@ -126,6 +126,84 @@ __device__ __forceinline__ void warp_layer(const __half *sAin, const __half *sWl
     }
 }
 
+// Stage the visibilities [c0, c0 + cnt) of item `it` (bin `bin`, L taps):
+// exact coordinates (FP64), flipped and weighted values; the weight sum and
+// the non-finite count are reduced over the block and added to the plan's
+// statistics.  All threads of the block call it.
+template <int NPOL>
+__device__ void stage_chunk(const LearnArgs &a, int4 it, int c0, int cnt, int L, int bin, VisL *sv, double *s_red) {
+    constexpr int P = NPOL * NPOL;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double wloc = 0.0;
+    unsigned long long nbad = 0;
+    for (int i = tid; i < cnt; i += blockDim.x) {
+        const aw_rec r = a.rec[it.x + c0 + i];
+        const uint32_t row = a.row[r.orig];
+        const uint16_t ch = a.chan[r.orig];
+        const double fq = a.freq[ch];
+        const double fl = fq / AW_C_LIGHT;
+        double u = a.uvw[3 * (int64_t)row] * fl, v = a.uvw[3 * (int64_t)row + 1] * fl;
+        double w = a.uvw[3 * (int64_t)row + 2] * fl;
+        if (w < 0) { u = -u; v = -v; w = -w; }
+        VisL e;
+        e.dx = (float)(u * a.cells_per_lambda + a.half_cells - (double)r.x0);
+        e.dy = (float)(v * a.cells_per_lambda + a.half_cells - (double)r.y0);
+        e.w = (float)w;
+        {
+            int pn = a.w_max > 0 ? (int)floor(w * a.norm_nw / a.w_max) : 0;
+            pn = min(max(pn, 0), a.norm_nw - 1);
+            e.inv_off = (float)(1.0 / (a.D * (a.norm[pn] / 2 + 1)));
+        }
+        e.pad1 = 0;
+        // the beam frequency of the visibility's bin: the network was
+        // trained at the bin centres (the exact path averages the beam
+        // over the same channel range)
+        e.f = (float)a.pa_centres[a.npa + bin % a.nfb];
+        e.pos = (int)r.x0 | ((int)r.y0 << 16);
+        e.koff = ((int)r.fy * a.OS + (int)r.fx) * L * P;
+        float2 vv[4] = {};
+        float ww[4] = {0, 0, 0, 0};
+        bool bad = false;
+        for (int c = 0; c < NPOL; ++c) {
+            vv[c] = a.vis[(int64_t)r.orig * NPOL + c];
+            ww[c] = a.weight ? a.weight[(int64_t)r.orig * NPOL + c] : 1.f;
+            bad |= !isfinite(vv[c].x) || !isfinite(vv[c].y) || !isfinite(ww[c]);
+        }
+        if (r.flip) {
+            for (int c = 0; c < NPOL; ++c) vv[c].y = -vv[c].y;
+            if (NPOL == 4) {
+                float2 t = vv[1]; vv[1] = vv[2]; vv[2] = t;
+                float tw = ww[1]; ww[1] = ww[2]; ww[2] = tw;
+            }
+        }
+        if (bad) {
+            nbad++;
+            for (int c = 0; c < NPOL; ++c) { vv[c] = make_float2(0.f, 0.f); ww[c] = 0.f; }
+        }
+        double wm = 0;
+        for (int c = 0; c < 4; ++c) {
+            e.v[c] = (c < NPOL) ? make_float2(ww[c] * vv[c].x, ww[c] * vv[c].y) : make_float2(0.f, 0.f);
+            if (c < NPOL) wm += ww[c];
+        }
+        wloc += wm / NPOL;
+        sv[i] = e;
+    }
+    for (int o = 16; o; o >>= 1) {
+        wloc += __shfl_xor_sync(0xffffffffu, wloc, o);
+        nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
+    }
+    if (lane == 0) {
+        s_red[warp] = wloc;
+        if (nbad) atomicAdd(a.nonfinite, nbad);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0;
+        for (int w = 0; w < LWARPS; ++w) t += s_red[w];
+        atomicAdd(a.wsum, t);
+    }
+}
+
 template <int NPOL>
 __global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
     constexpr int P = NPOL * NPOL;
@@ -138,7 +216,7 @@ __global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
     float *sW1 = reinterpret_cast<float *>(sAct + LWARPS * 2 * 16 * LPAD);  // [LW][5]
     float *sB = sW1 + LW * 5;                                   // [4][LW] hidden biases, then [NOUT]
     VisL *sv = reinterpret_cast<VisL *>(sB + 4 * LW + NOUT);    // [LCHUNK]
-    __shared__ int s_item, s_cnt;
+    __shared__ int s_item;
     __shared__ double s_red[LWARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -179,75 +257,7 @@ __global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
         for (int c0 = 0; c0 < it.y; c0 += LCHUNK) {
             const int cnt = min(LCHUNK, it.y - c0);
             __syncthreads();
-            // ---- stage: exact coordinates (FP64), flipped and weighted values
-            double wloc = 0.0;
-            unsigned long long nbad = 0;
-            for (int i = tid; i < cnt; i += blockDim.x) {
-                const aw_rec r = a.rec[it.x + c0 + i];
-                const uint32_t row = a.row[r.orig];
-                const uint16_t ch = a.chan[r.orig];
-                const double fq = a.freq[ch];
-                const double fl = fq / AW_C_LIGHT;
-                double u = a.uvw[3 * (int64_t)row] * fl, v = a.uvw[3 * (int64_t)row + 1] * fl;
-                double w = a.uvw[3 * (int64_t)row + 2] * fl;
-                if (w < 0) { u = -u; v = -v; w = -w; }
-                VisL e;
-                e.dx = (float)(u * a.cells_per_lambda + a.half_cells - (double)r.x0);
-                e.dy = (float)(v * a.cells_per_lambda + a.half_cells - (double)r.y0);
-                e.w = (float)w;
-                {
-                    int pn = a.w_max > 0 ? (int)floor(w * a.norm_nw / a.w_max) : 0;
-                    pn = min(max(pn, 0), a.norm_nw - 1);
-                    e.inv_off = (float)(1.0 / (a.D * (a.norm[pn] / 2 + 1)));
-                }
-                e.pad1 = 0;
-                // the beam frequency of the visibility's bin: the network was
-                // trained at the bin centres (the exact path averages the beam
-                // over the same channel range)
-                e.f = (float)a.pa_centres[a.npa + bin % a.nfb];
-                e.pos = (int)r.x0 | ((int)r.y0 << 16);
-                e.koff = ((int)r.fy * a.OS + (int)r.fx) * L * P;
-                float2 vv[4] = {};
-                float ww[4] = {0, 0, 0, 0};
-                bool bad = false;
-                for (int c = 0; c < NPOL; ++c) {
-                    vv[c] = a.vis[(int64_t)r.orig * NPOL + c];
-                    ww[c] = a.weight ? a.weight[(int64_t)r.orig * NPOL + c] : 1.f;
-                    bad |= !isfinite(vv[c].x) || !isfinite(vv[c].y) || !isfinite(ww[c]);
-                }
-                if (r.flip) {
-                    for (int c = 0; c < NPOL; ++c) vv[c].y = -vv[c].y;
-                    if (NPOL == 4) {
-                        float2 t = vv[1]; vv[1] = vv[2]; vv[2] = t;
-                        float tw = ww[1]; ww[1] = ww[2]; ww[2] = tw;
-                    }
-                }
-                if (bad) {
-                    nbad++;
-                    for (int c = 0; c < NPOL; ++c) { vv[c] = make_float2(0.f, 0.f); ww[c] = 0.f; }
-                }
-                double wm = 0;
-                for (int c = 0; c < 4; ++c) {
-                    e.v[c] = (c < NPOL) ? make_float2(ww[c] * vv[c].x, ww[c] * vv[c].y) : make_float2(0.f, 0.f);
-                    if (c < NPOL) wm += ww[c];
-                }
-                wloc += wm / NPOL;
-                sv[i] = e;
-            }
-            for (int o = 16; o; o >>= 1) {
-                wloc += __shfl_xor_sync(0xffffffffu, wloc, o);
-                nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
-            }
-            if (lane == 0) {
-                s_red[warp] = wloc;
-                if (nbad) atomicAdd(a.nonfinite, nbad);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0;
-                for (int w = 0; w < LWARPS; ++w) t += s_red[w];
-                atomicAdd(a.wsum, t);
-            }
+            stage_chunk<NPOL>(a, it, c0, cnt, L, bin, sv, s_red);
             // ---- points of this chunk, 16 rows per warp-tile
             const int npts = cnt * L;
             for (int t0 = warp * 16; t0 < npts; t0 += LWARPS * 16) {
@@ -367,6 +377,335 @@ __global__ void __launch_bounds__(256, 1) grid_learned_kernel(LearnArgs a) {
     }
 }
 
+// ============================================================================
+// The same gridding with the network on the 5th-generation tensor cores.
+//
+// A CTA pushes tiles of 128 (visibility, tap) rows through the network: the
+// FP16 activations of a tile (A) and the FP16 weights of every layer (B) sit
+// in shared memory in the canonical K-major layout without swizzle (8 x 8
+// core matrices of 128 contiguous bytes; 128 B to the next core matrix along
+// K, 2048 B to the next group of 8 rows), one thread issues
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, K = 16 per instruction) with
+// the FP32 accumulator in tensor memory, tcgen05.commit signals an mbarrier,
+// and the 8 warps read the accumulator back with tcgen05.ld (warp w reaches
+// TMEM lanes 32 (w % 4) ..), add the bias, take the sine and store the next
+// layer's FP16 operand.  After the output layer each row's thread holds the
+// P complex Mueller values of its tap and adds the product with the
+// visibility to the grid.  Every mbarrier wait is bounded: a wait that runs
+// out sets the error word, and the CTA leaves its loops, frees its tensor
+// memory and returns.
+namespace tc {
+
+constexpr int TM = 128;                      // rows per tile (MMA M)
+constexpr int KCM = LW / 8;                  // core matrices along K (16)
+constexpr int TILE_BYTES = TM * LW * 2;      // 32 KB: a 128 x 128 FP16 operand
+constexpr uint32_t TMEM_COLS = 256;          // hidden accumulator [0, 128), output [128, 128 + NOUT)
+constexpr long long WAIT_LIMIT = 1ll << 22;  // mbarrier polls (with back-off) before giving up
+
+// byte offset of element (row r, k) of a K-major core-matrix operand with LW columns
+__device__ __forceinline__ uint32_t cm_off(int r, int k) {
+    return (uint32_t)(((r >> 3) * KCM + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start >> 4 [0,14), LBO >> 4 [16,30),
+// SBO >> 4 [32,46), version 1 [46,48), no swizzle [61,64)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(2048u >> 4) << 32) |
+           (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D F32 [4,6) = 1, A = B = F16 (0), both
+// K-major, N >> 3 at [17,23), M >> 4 at [24,29)
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_smem_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with parity `parity`; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try(mbar, parity)) return true;
+        if (i > 64) __nanosleep(128);
+    }
+    return false;
+}
+
+// 8 FP16 values of row r, columns [k0, k0 + 8), into the operand tile
+__device__ __forceinline__ void st8(unsigned char *tile, int r, int k0, const float (&x)[8]) {
+    uint4 q;
+    __half2 h0 = __floats2half2_rn(x[0], x[1]), h1 = __floats2half2_rn(x[2], x[3]);
+    __half2 h2 = __floats2half2_rn(x[4], x[5]), h3 = __floats2half2_rn(x[6], x[7]);
+    q.x = *reinterpret_cast<uint32_t *>(&h0);
+    q.y = *reinterpret_cast<uint32_t *>(&h1);
+    q.z = *reinterpret_cast<uint32_t *>(&h2);
+    q.w = *reinterpret_cast<uint32_t *>(&h3);
+    *reinterpret_cast<uint4 *>(tile + cm_off(r, k0)) = q;
+}
+
+}  // namespace tc
+
+template <int NPOL>
+struct TcDims {
+    static constexpr int P = NPOL * NPOL;
+    static constexpr int NOUT = (2 * P + 15) / 16 * 16;   // 32 (full pol) or 16 (Stokes I): MMA N
+    static constexpr size_t W_OFF = 0;                                  // 3 hidden layers, 32 KB each
+    static constexpr size_t WO_OFF = 3 * (size_t)tc::TILE_BYTES;        // output layer [NOUT][LW]
+    static constexpr size_t A_OFF = WO_OFF + (size_t)NOUT * LW * 2;     // activation tile
+    static constexpr size_t W1_OFF = A_OFF + tc::TILE_BYTES;            // float [LW][5]
+    static constexpr size_t B_OFF = W1_OFF + (size_t)LW * 5 * 4;        // float [4][LW], then [NOUT]
+    static constexpr size_t SV_OFF = (B_OFF + (size_t)(4 * LW + NOUT) * 4 + 15) / 16 * 16;
+    static constexpr size_t BYTES = SV_OFF + (size_t)LCHUNK * sizeof(VisL);
+};
+
+template <int NPOL>
+__global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, unsigned int *err) {
+    using Dm = TcDims<NPOL>;
+    constexpr int P = Dm::P;
+    constexpr int NOUT = Dm::NOUT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *sW = smem + Dm::W_OFF;
+    unsigned char *sWo = smem + Dm::WO_OFF;
+    unsigned char *sA = smem + Dm::A_OFF;
+    float *sW1 = reinterpret_cast<float *>(smem + Dm::W1_OFF);
+    float *sB = reinterpret_cast<float *>(smem + Dm::B_OFF);
+    VisL *sv = reinterpret_cast<VisL *>(smem + Dm::SV_OFF);
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_item, s_abort;
+    __shared__ double s_red[LWARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---- weights into the operand layouts once
+    for (int l = 0; l < 3; ++l)
+        for (int i = tid; i < LW * LW; i += blockDim.x) {
+            const int o = i / LW, k = i % LW;
+            *reinterpret_cast<__half *>(sW + (size_t)l * tc::TILE_BYTES + tc::cm_off(o, k)) = a.Wh[a.woff[l + 1] + i];
+        }
+    for (int i = tid; i < NOUT * LW; i += blockDim.x) {
+        const int o = i / LW, k = i % LW;
+        *reinterpret_cast<__half *>(sWo + tc::cm_off(o, k)) =
+            (o < 2 * P) ? a.Wh[a.woff[4] + (int64_t)o * LW + k] : __float2half(0.f);
+    }
+    for (int i = tid; i < LW * 5; i += blockDim.x) sW1[i] = a.Wf[a.woff[0] + i];
+    for (int i = tid; i < 4 * LW; i += blockDim.x) sB[i] = a.Wf[a.boff[i / LW] + (i % LW)];
+    for (int i = tid; i < NOUT; i += blockDim.x) sB[4 * LW + i] = (i < 2 * P) ? a.Wf[a.boff[4] + i] : 0.f;
+    const uint32_t mbar = tc::su32(&s_mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::su32(&s_tmem)),
+                     "r"(tc::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc::fence_smem_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t acc_h = tmem;          // hidden-layer accumulator, columns [0, 128)
+    const uint32_t acc_o = tmem + 128;    // output-layer accumulator
+    const uint32_t id_h = tc::idesc(tc::TM, LW), id_o = tc::idesc(tc::TM, NOUT);
+    const uint32_t aA = tc::su32(sA), aW = tc::su32(sW), aWo = tc::su32(sWo);
+    uint32_t phase = 0;
+    // the TMEM lanes (rows) and accumulator columns this warp reads back
+    const int row = 32 * (warp & 3) + lane;
+    const int colh = 64 * (warp >> 2);
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.nitems || s_abort) break;
+        const int4 it = a.items[item];
+        const int bin = it.z;
+        const int S = a.bin_support[bin];
+        const int L = S * S;
+        const int plane = bin / (a.npa * a.nfb);
+        const int pab = (bin / a.nfb) % a.npa;
+        const bool rejected = a.plane_rejected && a.plane_rejected[plane];
+        const float chi_feat = (float)((a.pa_centres[pab] - a.chi_c) * a.inv_chi_h);
+        const int64_t tab0 = a.bin_offset ? a.bin_offset[bin] : 0;
+        for (int c0 = 0; c0 < it.y && !s_abort; c0 += LCHUNK) {
+            const int cnt = min(LCHUNK, it.y - c0);
+            __syncthreads();
+            stage_chunk<NPOL>(a, it, c0, cnt, L, bin, sv, s_red);
+            __syncthreads();
+            const int npts = cnt * L;
+            for (int t0 = 0; t0 < npts; t0 += tc::TM) {
+                // this thread's row for layer 1 and, in warps 0-3, for the output step
+                const int p = t0 + (tid & (tc::TM - 1));
+                const bool okp = p < npts;
+                const int vi = okp ? p / L : 0;
+                const int tp = okp ? p - vi * L : 0;
+                const int jy = tp / S, jx = tp - (tp / S) * S;
+                float kv[2 * P];
+                if (!rejected) {
+                    // layer 1 (5 -> 128) in FP32: two threads per row, 64 outputs each
+                    {
+                        float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                        if (okp) {
+                            x[0] = ((float)jx - sv[vi].dx) * sv[vi].inv_off;
+                            x[1] = ((float)jy - sv[vi].dy) * sv[vi].inv_off;
+                            x[2] = sv[vi].w * a.w_scale - 1.f;
+                            x[3] = (sv[vi].f - a.f_c) * a.inv_f_h;
+                            x[4] = chi_feat;
+                        }
+                        const int r = tid & (tc::TM - 1), o0 = (tid >> 7) * 64;
+                        for (int g = 0; g < 8; ++g) {
+                            float h[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int o = o0 + g * 8 + e;
+                                float z = sB[o];
+#pragma unroll
+                                for (int k = 0; k < 5; ++k) z = fmaf(sW1[o * 5 + k], x[k], z);
+                                h[e] = __sinf(a.omega0 * z);
+                            }
+                            tc::st8(sA, r, o0 + g * 8, h);
+                        }
+                    }
+                    tc::fence_smem_async();
+                    tc::fence_before();
+                    __syncthreads();
+                    // layers 2..4 and the output layer
+                    for (int l = 0; l < 4; ++l) {
+                        const bool out_layer = (l == 3);
+                        if (tid == 0) {
+                            tc::fence_after();
+                            const uint32_t wb = out_layer ? aWo : aW + (uint32_t)l * tc::TILE_BYTES;
+#pragma unroll
+                            for (int ks = 0; ks < LW / 16; ++ks)
+                                tc::mma(out_layer ? acc_o : acc_h, tc::sdesc(aA + ks * 256), tc::sdesc(wb + ks * 256),
+                                        out_layer ? id_o : id_h, ks > 0 ? 1u : 0u);
+                            tc::commit(mbar);
+                        }
+                        const bool done = tc::mbar_wait(mbar, phase);
+                        phase ^= 1u;
+                        if (!done) {
+                            atomicExch(err, 1u);
+                            s_abort = 1;
+                        }
+                        tc::fence_after();
+                        if (!out_layer) {
+                            // read back 64 columns of this warp's 32 rows, bias, sine, FP16 operand
+#pragma unroll
+                            for (int half = 0; half < 2; ++half) {
+                                float v[32];
+                                tc::ld32(acc_h + lane_base + colh + 32 * half, v);
+#pragma unroll
+                                for (int g = 0; g < 4; ++g) {
+                                    float h[8];
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e) {
+                                        const int c = colh + 32 * half + g * 8 + e;
+                                        h[e] = __sinf(a.omega0 * (v[g * 8 + e] + sB[(l + 1) * LW + c]));
+                                    }
+                                    tc::st8(sA, row, colh + 32 * half + g * 8, h);
+                                }
+                            }
+                            tc::fence_smem_async();
+                        } else if (warp < 4) {
+                            float v[32];
+                            tc::ld32(acc_o + lane_base, v);
+#pragma unroll
+                            for (int i = 0; i < 2 * P; ++i) kv[i] = (v[i] + sB[4 * LW + i]) * a.out_scale;
+                        }
+                        tc::fence_before();
+                        __syncthreads();
+                        if (s_abort) break;
+                    }
+                    if (s_abort) break;
+                } else if (warp < 4) {
+                    // rejected plane: the exact table values at the quantised offset
+#pragma unroll
+                    for (int m = 0; m < P; ++m) {
+                        float2 k = make_float2(0.f, 0.f);
+                        if (okp) k = read_tab(a.ktab, a.storage, tab0 + sv[vi].koff + aw_tab_index(a.ce, L, tp, m));
+                        kv[2 * m] = k.x * a.inv_kscale;
+                        kv[2 * m + 1] = k.y * a.inv_kscale;
+                    }
+                }
+                // apply to the visibility and add to the grid: warps 0-3, one row each
+                if (warp < 4 && okp) {
+                    const int pos = sv[vi].pos;
+                    const int gx = (pos & 0xffff) + jx, gy = (pos >> 16) + jy;
+#pragma unroll
+                    for (int so = 0; so < NPOL; ++so) {
+                        float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c) {
+                            const float kr = kv[2 * (so * NPOL + c)], ki = kv[2 * (so * NPOL + c) + 1];
+                            const float2 vq = sv[vi].v[c];
+                            o.x += kr * vq.x - ki * vq.y;
+                            o.y += kr * vq.y + ki * vq.x;
+                        }
+                        atomicAdd(a.grid + ((int64_t)so * a.N + gy) * a.N + gx, o);
+                    }
+                }
+                if (rejected) __syncthreads();
+            }
+        }
+    }
+    // ---- free the tensor memory (all MMAs have completed: every commit was waited for)
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tc::TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 size_t aw_learned_smem_bytes(int npol) {
@@ -428,11 +767,32 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
     a.wsum = p->d_wsum;
     a.nonfinite = p->d_nonfinite;
     a.counter = p->d_counter;
-    const size_t smem = aw_learned_smem_bytes(p->npol);
     AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), st));
     AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), st));
     AW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st));
     const int ctas = (int)std::min<int64_t>(p->nitems, sm_count);
+    if (s->engine == AW_ENGINE_TCGEN05) {
+        if (!s->d_err) AW_CUDA_TRY(cudaMalloc(&s->d_err, sizeof(unsigned int)));
+        AW_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned int), st));
+        if (p->npol == 4) {
+            const size_t sm4 = TcDims<4>::BYTES;
+            AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm4));
+            grid_learned_tc_kernel<4><<<ctas, 256, sm4, st>>>(a, s->d_err);
+        } else {
+            const size_t sm1 = TcDims<1>::BYTES;
+            AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm1));
+            grid_learned_tc_kernel<1><<<ctas, 256, sm1, st>>>(a, s->d_err);
+        }
+        AW_CHECK_LAUNCH();
+        unsigned int e = 0;
+        AW_CUDA_TRY(cudaMemcpyAsync(&e, s->d_err, sizeof(e), cudaMemcpyDeviceToHost, st));
+        AW_CUDA_TRY(cudaStreamSynchronize(st));
+        if (e) return aw_set_error(AW_ETIMEOUT, "grid_learned: a tensor-core completion wait gave up; grid invalid");
+        return AW_OK;
+    }
+    const size_t smem = aw_learned_smem_bytes(p->npol);
     if (p->npol == 4) {
         AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         grid_learned_kernel<4><<<ctas, 256, smem, st>>>(a);

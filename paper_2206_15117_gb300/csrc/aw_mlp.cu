@@ -621,6 +621,7 @@ int aw_sur_init(aw_surrogate *s) {
 void aw_sur_free(aw_surrogate *s) {
     for (float *p : s->work) cudaFree(p);
     if (s->d_rejected) cudaFree(s->d_rejected);
+    if (s->d_err) cudaFree(s->d_err);
     if (s->d_pa) cudaFree(s->d_pa);
     if (s->d_norm) cudaFree(s->d_norm);
     if (s->d_p) cudaFree(s->d_p);

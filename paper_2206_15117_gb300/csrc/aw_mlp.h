@@ -27,6 +27,9 @@ struct aw_surrogate {
     // offset-normalisation plane layout (host copy and device copy)
     std::vector<int32_t> norm;
     int32_t *d_norm = nullptr;
+    // tensor-core engine of the inline evaluation (AW_ENGINE_*) and its error word
+    int engine = AW_ENGINE_TCGEN05;
+    unsigned int *d_err = nullptr;
 };
 
 int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,

@@ -185,6 +185,13 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *s, const aw_kernel_set *exact
     SUR_GUARD_END
 }
 
+int aw_surrogate_set_engine(aw_surrogate *s, int32_t engine) {
+    if (!s) return aw_set_error(AW_EINVAL, "surrogate is NULL");
+    if (engine != AW_ENGINE_MMA_SYNC && engine != AW_ENGINE_TCGEN05) return aw_set_error(AW_EINVAL, "engine %d", engine);
+    s->engine = engine;
+    return AW_OK;
+}
+
 }  // extern "C"
 
 extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback,

@@ -34,9 +34,11 @@ def _setup(ctx, n_t=10):
     return ob, kw, exact, sur, plan, vis, w, scales, (vd, keep)
 
 
-def test_inline_surrogate_gridding_matches_oracle(ctx):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_inline_surrogate_gridding_matches_oracle(ctx, engine):
     from paper_2206_15117_gb300 import aw
     ob, kw, exact, sur, plan, vis, w, scales, keep = _setup(ctx)
+    aw.aw_surrogate_set_engine(sur, engine)
     grid = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
     st = aw.aw_grid_learned(ctx, plan, sur, exact, torch.as_tensor(vis, device="cuda"),
                             torch.as_tensor(w, device="cuda"), grid, want_stats=True)
@@ -58,9 +60,11 @@ def test_inline_surrogate_gridding_matches_oracle(ctx):
     assert st.weight_sum == pytest.approx(ws, rel=1e-12)
 
 
-def test_rejected_planes_fall_back_to_exact_tables(ctx):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_rejected_planes_fall_back_to_exact_tables(ctx, engine):
     from paper_2206_15117_gb300 import aw
     ob, kw, exact, sur, plan, vis, w, scales, keep = _setup(ctx)
+    aw.aw_surrogate_set_engine(sur, engine)
     learned, err, nrej = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=0.0)   # reject every plane
     assert nrej == aw.aw_kernel_set_info(exact).nbins
     grid = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
@@ -70,3 +74,21 @@ def test_rejected_planes_fall_back_to_exact_tables(ctx):
     G, _, _ = oc.grid(oc.make_kernels(oracle_spec(kw), bins=used_bins(co)), co, vis, w)
     l2, mx = rel_err(grid.cpu().numpy(), G)
     assert l2 < TOL_FP32 and mx < TOL_FP32, (l2, mx)
+
+
+def test_tensor_core_engines_agree(ctx):
+    # the two tensor-core engines run the same FP16 network with FP32 accumulation:
+    # they differ by FP32 summation order and occasional FP16 roundings of activations
+    from paper_2206_15117_gb300 import aw
+    ob, kw, exact, sur, plan, vis, w, scales, keep = _setup(ctx, n_t=16)
+    out = []
+    for engine in (aw.AW_ENGINE_MMA_SYNC, aw.AW_ENGINE_TCGEN05):
+        aw.aw_surrogate_set_engine(sur, engine)
+        grid = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
+        aw.aw_grid_learned(ctx, plan, sur, exact, torch.as_tensor(vis, device="cuda"),
+                           torch.as_tensor(w, device="cuda"), grid)
+        out.append(grid.cpu().numpy())
+    l2, mx = rel_err(out[1], out[0])
+    assert l2 < 2e-3, (l2, mx)
+    with pytest.raises(RuntimeError):
+        aw.aw_surrogate_set_engine(sur, 7)
