@@ -399,7 +399,7 @@ namespace tc {
 constexpr int TM = 128;                      // rows per tile (MMA M)
 constexpr int KCM = LW / 8;                  // core matrices along K (16)
 constexpr int TILE_BYTES = TM * LW * 2;      // 32 KB: a 128 x 128 FP16 operand
-constexpr uint32_t TMEM_COLS = 256;          // hidden accumulator [0, 128), output [128, 128 + NOUT)
+constexpr uint32_t TMEM_COLS = 512;          // per warpgroup g: hidden [128 g, +128), output [256 + 32 g, +32)
 constexpr long long WAIT_LIMIT = 1ll << 22;  // mbarrier polls (with back-off) before giving up
 
 // byte offset of element (row r, k) of a K-major core-matrix operand with LW columns
@@ -494,13 +494,21 @@ struct TcDims {
     static constexpr int NOUT = (2 * P + 15) / 16 * 16;   // 32 (full pol) or 16 (Stokes I): MMA N
     static constexpr size_t W_OFF = 0;                                  // 3 hidden layers, 32 KB each
     static constexpr size_t WO_OFF = 3 * (size_t)tc::TILE_BYTES;        // output layer [NOUT][LW]
-    static constexpr size_t A_OFF = WO_OFF + (size_t)NOUT * LW * 2;     // activation tile
-    static constexpr size_t W1_OFF = A_OFF + tc::TILE_BYTES;            // float [LW][5]
-    static constexpr size_t B_OFF = W1_OFF + (size_t)LW * 5 * 4;        // float [4][LW], then [NOUT]
+    static constexpr size_t A_OFF = WO_OFF + (size_t)NOUT * LW * 2;     // 2 activation tiles (one per warpgroup)
+    static constexpr size_t W1_OFF = A_OFF + 2 * (size_t)tc::TILE_BYTES;  // float [LW][5]
+    static constexpr size_t B_OFF = W1_OFF + (size_t)LW * 5 * 4;        // float [4][LW] omega0 x bias, then [NOUT] bias
     static constexpr size_t SV_OFF = (B_OFF + (size_t)(4 * LW + NOUT) * 4 + 15) / 16 * 16;
     static constexpr size_t BYTES = SV_OFF + (size_t)LCHUNK * sizeof(VisL);
 };
 
+__device__ __forceinline__ void wg_sync(int wg) {
+    asm volatile("bar.sync %0, 128;\n" ::"r"(1 + wg) : "memory");
+}
+
+// The two warpgroups of the CTA work on alternate tiles of a chunk, each with
+// its own activation tile, accumulator columns and mbarrier, and an elected
+// thread of each issues its own MMAs: while one warpgroup runs an epilogue
+// the tensor cores work on the other's layer.
 template <int NPOL>
 __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, unsigned int *err) {
     using Dm = TcDims<NPOL>;
@@ -509,15 +517,16 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *sW = smem + Dm::W_OFF;
     unsigned char *sWo = smem + Dm::WO_OFF;
-    unsigned char *sA = smem + Dm::A_OFF;
     float *sW1 = reinterpret_cast<float *>(smem + Dm::W1_OFF);
     float *sB = reinterpret_cast<float *>(smem + Dm::B_OFF);
     VisL *sv = reinterpret_cast<VisL *>(smem + Dm::SV_OFF);
-    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ __align__(8) unsigned long long s_mbar[2];
     __shared__ uint32_t s_tmem;
-    __shared__ int s_item, s_abort;
+    __shared__ int s_item, s_abort, s_wgab[2];
     __shared__ double s_red[LWARPS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int wg = warp >> 2, wtid = tid & 127;          // warpgroup, thread within it (= tile row)
+    unsigned char *sA = smem + Dm::A_OFF + (size_t)wg * tc::TILE_BYTES;
 
     // ---- weights into the operand layouts once
     for (int l = 0; l < 3; ++l)
@@ -531,13 +540,17 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
             (o < 2 * P) ? a.Wh[a.woff[4] + (int64_t)o * LW + k] : __float2half(0.f);
     }
     for (int i = tid; i < LW * 5; i += blockDim.x) sW1[i] = a.Wf[a.woff[0] + i];
-    for (int i = tid; i < 4 * LW; i += blockDim.x) sB[i] = a.Wf[a.boff[i / LW] + (i % LW)];
+    for (int i = tid; i < 4 * LW; i += blockDim.x) {
+        const float b = a.Wf[a.boff[i / LW] + (i % LW)];
+        sB[i] = (i < LW) ? b : a.omega0 * b;   // layer 1 keeps the plain bias (FP32 layer)
+    }
     for (int i = tid; i < NOUT; i += blockDim.x) sB[4 * LW + i] = (i < 2 * P) ? a.Wf[a.boff[4] + i] : 0.f;
-    const uint32_t mbar = tc::su32(&s_mbar);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        for (int g = 0; g < 2; ++g)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::su32(&s_mbar[g])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
+        s_wgab[0] = s_wgab[1] = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::su32(&s_tmem)),
@@ -550,14 +563,12 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t acc_h = tmem;          // hidden-layer accumulator, columns [0, 128)
-    const uint32_t acc_o = tmem + 128;    // output-layer accumulator
+    const uint32_t acc_h = tmem + (uint32_t)wg * 128;        // hidden accumulator of this warpgroup
+    const uint32_t acc_o = tmem + 256 + (uint32_t)wg * 32;   // output accumulator of this warpgroup
     const uint32_t id_h = tc::idesc(tc::TM, LW), id_o = tc::idesc(tc::TM, NOUT);
     const uint32_t aA = tc::su32(sA), aW = tc::su32(sW), aWo = tc::su32(sWo);
+    const uint32_t mbar = tc::su32(&s_mbar[wg]);
     uint32_t phase = 0;
-    // the TMEM lanes (rows) and accumulator columns this warp reads back
-    const int row = 32 * (warp & 3) + lane;
-    const int colh = 64 * (warp >> 2);
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
 
     for (;;) {
@@ -581,16 +592,16 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
             stage_chunk<NPOL>(a, it, c0, cnt, L, bin, sv, s_red);
             __syncthreads();
             const int npts = cnt * L;
-            for (int t0 = 0; t0 < npts; t0 += tc::TM) {
-                // this thread's row for layer 1 and, in warps 0-3, for the output step
-                const int p = t0 + (tid & (tc::TM - 1));
+            // this warpgroup's tiles: 2k + wg
+            for (int t0 = wg * tc::TM; t0 < npts; t0 += 2 * tc::TM) {
+                const int p = t0 + wtid;
                 const bool okp = p < npts;
                 const int vi = okp ? p / L : 0;
                 const int tp = okp ? p - vi * L : 0;
                 const int jy = tp / S, jx = tp - (tp / S) * S;
                 float kv[2 * P];
                 if (!rejected) {
-                    // layer 1 (5 -> 128) in FP32: two threads per row, 64 outputs each
+                    // layer 1 (5 -> 128) in FP32, one row per thread
                     {
                         float x[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
                         if (okp) {
@@ -600,27 +611,26 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
                             x[3] = (sv[vi].f - a.f_c) * a.inv_f_h;
                             x[4] = chi_feat;
                         }
-                        const int r = tid & (tc::TM - 1), o0 = (tid >> 7) * 64;
-                        for (int g = 0; g < 8; ++g) {
+                        for (int g = 0; g < LW / 8; ++g) {
                             float h[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
-                                const int o = o0 + g * 8 + e;
+                                const int o = g * 8 + e;
                                 float z = sB[o];
 #pragma unroll
                                 for (int k = 0; k < 5; ++k) z = fmaf(sW1[o * 5 + k], x[k], z);
                                 h[e] = __sinf(a.omega0 * z);
                             }
-                            tc::st8(sA, r, o0 + g * 8, h);
+                            tc::st8(sA, wtid, g * 8, h);
                         }
                     }
                     tc::fence_smem_async();
                     tc::fence_before();
-                    __syncthreads();
+                    wg_sync(wg);
                     // layers 2..4 and the output layer
                     for (int l = 0; l < 4; ++l) {
                         const bool out_layer = (l == 3);
-                        if (tid == 0) {
+                        if (wtid == 0) {
                             tc::fence_after();
                             const uint32_t wb = out_layer ? aWo : aW + (uint32_t)l * tc::TILE_BYTES;
 #pragma unroll
@@ -633,39 +643,39 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
                         phase ^= 1u;
                         if (!done) {
                             atomicExch(err, 1u);
-                            s_abort = 1;
+                            s_wgab[wg] = 1;
                         }
                         tc::fence_after();
                         if (!out_layer) {
-                            // read back 64 columns of this warp's 32 rows, bias, sine, FP16 operand
+                            // this row's 128 columns: omega0 (acc + bias), sine, FP16 operand
+                            const float *bw = sB + (l + 1) * LW;
 #pragma unroll
-                            for (int half = 0; half < 2; ++half) {
+                            for (int q = 0; q < 4; ++q) {
                                 float v[32];
-                                tc::ld32(acc_h + lane_base + colh + 32 * half, v);
+                                tc::ld32(acc_h + lane_base + 32 * q, v);
 #pragma unroll
                                 for (int g = 0; g < 4; ++g) {
                                     float h[8];
 #pragma unroll
                                     for (int e = 0; e < 8; ++e) {
-                                        const int c = colh + 32 * half + g * 8 + e;
-                                        h[e] = __sinf(a.omega0 * (v[g * 8 + e] + sB[(l + 1) * LW + c]));
+                                        const int c = 32 * q + g * 8 + e;
+                                        h[e] = __sinf(fmaf(a.omega0, v[g * 8 + e], bw[c]));
                                     }
-                                    tc::st8(sA, row, colh + 32 * half + g * 8, h);
+                                    tc::st8(sA, wtid, 32 * q + g * 8, h);
                                 }
                             }
                             tc::fence_smem_async();
-                        } else if (warp < 4) {
+                        } else {
                             float v[32];
                             tc::ld32(acc_o + lane_base, v);
 #pragma unroll
                             for (int i = 0; i < 2 * P; ++i) kv[i] = (v[i] + sB[4 * LW + i]) * a.out_scale;
                         }
                         tc::fence_before();
-                        __syncthreads();
-                        if (s_abort) break;
+                        wg_sync(wg);
+                        if (s_wgab[wg]) break;   // read after the barrier: the same in every thread
                     }
-                    if (s_abort) break;
-                } else if (warp < 4) {
+                } else {
                     // rejected plane: the exact table values at the quantised offset
 #pragma unroll
                     for (int m = 0; m < P; ++m) {
@@ -675,8 +685,9 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
                         kv[2 * m + 1] = k.y * a.inv_kscale;
                     }
                 }
-                // apply to the visibility and add to the grid: warps 0-3, one row each
-                if (warp < 4 && okp) {
+                if (s_wgab[wg]) break;
+                // apply to the visibility and add to the grid, one row per thread
+                if (okp) {
                     const int pos = sv[vi].pos;
                     const int gx = (pos & 0xffff) + jx, gy = (pos >> 16) + jy;
 #pragma unroll
@@ -692,11 +703,13 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
                         atomicAdd(a.grid + ((int64_t)so * a.N + gy) * a.N + gx, o);
                     }
                 }
-                if (rejected) __syncthreads();
             }
+            __syncthreads();
+            if (tid == 0 && (s_wgab[0] || s_wgab[1])) s_abort = 1;
+            __syncthreads();   // s_abort is read by every thread in the loop conditions
         }
     }
-    // ---- free the tensor memory (all MMAs have completed: every commit was waited for)
+    // ---- free the tensor memory (every commit was waited for)
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
