@@ -199,7 +199,7 @@ __device__ void stage_chunk(const LearnArgs &a, int4 it, int c0, int cnt, int L,
     __syncthreads();
     if (tid == 0) {
         double t = 0;
-        for (int w = 0; w < LWARPS; ++w) t += s_red[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
         atomicAdd(a.wsum, t);
     }
 }
@@ -399,7 +399,7 @@ namespace tc {
 constexpr int TM = 128;                      // rows per tile (MMA M)
 constexpr int KCM = LW / 8;                  // core matrices along K (16)
 constexpr int TILE_BYTES = TM * LW * 2;      // 32 KB: a 128 x 128 FP16 operand
-constexpr uint32_t TMEM_COLS = 512;          // per warpgroup g: hidden [128 g, +128), output [256 + 32 g, +32)
+constexpr uint32_t TMEM_COLS = 512;          // 128 columns per warpgroup (at most 4)
 constexpr long long WAIT_LIMIT = 1ll << 22;  // mbarrier polls (with back-off) before giving up
 
 // byte offset of element (row r, k) of a K-major core-matrix operand with LW columns
@@ -494,8 +494,9 @@ struct TcDims {
     static constexpr int NOUT = (2 * P + 15) / 16 * 16;   // 32 (full pol) or 16 (Stokes I): MMA N
     static constexpr size_t W_OFF = 0;                                  // 3 hidden layers, 32 KB each
     static constexpr size_t WO_OFF = 3 * (size_t)tc::TILE_BYTES;        // output layer [NOUT][LW]
-    static constexpr size_t A_OFF = WO_OFF + (size_t)NOUT * LW * 2;     // 2 activation tiles (one per warpgroup)
-    static constexpr size_t W1_OFF = A_OFF + 2 * (size_t)tc::TILE_BYTES;  // float [LW][5]
+    static constexpr int NWG = 3;                                       // warpgroups (tiles in flight)
+    static constexpr size_t A_OFF = WO_OFF + (size_t)NOUT * LW * 2;     // one activation tile per warpgroup
+    static constexpr size_t W1_OFF = A_OFF + NWG * (size_t)tc::TILE_BYTES;  // float [LW][5]
     static constexpr size_t B_OFF = W1_OFF + (size_t)LW * 5 * 4;        // float [4][LW] omega0 x bias, then [NOUT] bias
     static constexpr size_t SV_OFF = (B_OFF + (size_t)(4 * LW + NOUT) * 4 + 15) / 16 * 16;
     static constexpr size_t BYTES = SV_OFF + (size_t)LCHUNK * sizeof(VisL);
@@ -505,13 +506,15 @@ __device__ __forceinline__ void wg_sync(int wg) {
     asm volatile("bar.sync %0, 128;\n" ::"r"(1 + wg) : "memory");
 }
 
-// The two warpgroups of the CTA work on alternate tiles of a chunk, each with
-// its own activation tile, accumulator columns and mbarrier, and an elected
-// thread of each issues its own MMAs: while one warpgroup runs an epilogue
-// the tensor cores work on the other's layer.
+// The NWG warpgroups of the CTA work on interleaved tiles of a chunk, each
+// with its own activation tile, 128 accumulator columns (the output layer
+// reuses the first 32 once the last hidden epilogue has read them) and
+// mbarrier, and an elected thread of each issues its own MMAs: while some
+// warpgroups run epilogues the tensor cores work on another's layer.
 template <int NPOL>
-__global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, unsigned int *err) {
+__global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_kernel(LearnArgs a, unsigned int *err) {
     using Dm = TcDims<NPOL>;
+    constexpr int NWG = Dm::NWG;
     constexpr int P = Dm::P;
     constexpr int NOUT = Dm::NOUT;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -520,10 +523,10 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
     float *sW1 = reinterpret_cast<float *>(smem + Dm::W1_OFF);
     float *sB = reinterpret_cast<float *>(smem + Dm::B_OFF);
     VisL *sv = reinterpret_cast<VisL *>(smem + Dm::SV_OFF);
-    __shared__ __align__(8) unsigned long long s_mbar[2];
+    __shared__ __align__(8) unsigned long long s_mbar[NWG];
     __shared__ uint32_t s_tmem;
-    __shared__ int s_item, s_abort, s_wgab[2];
-    __shared__ double s_red[LWARPS];
+    __shared__ int s_item, s_abort, s_wgab[NWG];
+    __shared__ double s_red[4 * NWG];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int wg = warp >> 2, wtid = tid & 127;          // warpgroup, thread within it (= tile row)
     unsigned char *sA = smem + Dm::A_OFF + (size_t)wg * tc::TILE_BYTES;
@@ -546,11 +549,12 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
     }
     for (int i = tid; i < NOUT; i += blockDim.x) sB[4 * LW + i] = (i < 2 * P) ? a.Wf[a.boff[4] + i] : 0.f;
     if (tid == 0) {
-        for (int g = 0; g < 2; ++g)
+        for (int g = 0; g < NWG; ++g) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::su32(&s_mbar[g])) : "memory");
+            s_wgab[g] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
-        s_wgab[0] = s_wgab[1] = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::su32(&s_tmem)),
@@ -563,8 +567,8 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t acc_h = tmem + (uint32_t)wg * 128;        // hidden accumulator of this warpgroup
-    const uint32_t acc_o = tmem + 256 + (uint32_t)wg * 32;   // output accumulator of this warpgroup
+    const uint32_t acc_h = tmem + (uint32_t)wg * 128;        // this warpgroup's accumulator columns
+    const uint32_t acc_o = acc_h;                            // the output layer (N <= 32) reuses them
     const uint32_t id_h = tc::idesc(tc::TM, LW), id_o = tc::idesc(tc::TM, NOUT);
     const uint32_t aA = tc::su32(sA), aW = tc::su32(sW), aWo = tc::su32(sWo);
     const uint32_t mbar = tc::su32(&s_mbar[wg]);
@@ -592,8 +596,8 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
             stage_chunk<NPOL>(a, it, c0, cnt, L, bin, sv, s_red);
             __syncthreads();
             const int npts = cnt * L;
-            // this warpgroup's tiles: 2k + wg
-            for (int t0 = wg * tc::TM; t0 < npts; t0 += 2 * tc::TM) {
+            // this warpgroup's tiles: NWG k + wg
+            for (int t0 = wg * tc::TM; t0 < npts; t0 += NWG * tc::TM) {
                 const int p = t0 + wtid;
                 const bool okp = p < npts;
                 const int vi = okp ? p / L : 0;
@@ -705,7 +709,9 @@ __global__ void __launch_bounds__(256, 1) grid_learned_tc_kernel(LearnArgs a, un
                 }
             }
             __syncthreads();
-            if (tid == 0 && (s_wgab[0] || s_wgab[1])) s_abort = 1;
+            if (tid == 0)
+                for (int g = 0; g < NWG; ++g)
+                    if (s_wgab[g]) s_abort = 1;
             __syncthreads();   // s_abort is read by every thread in the loop conditions
         }
     }
@@ -791,12 +797,12 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
             const size_t sm4 = TcDims<4>::BYTES;
             AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm4));
-            grid_learned_tc_kernel<4><<<ctas, 256, sm4, st>>>(a, s->d_err);
+            grid_learned_tc_kernel<4><<<ctas, 128 * TcDims<4>::NWG, sm4, st>>>(a, s->d_err);
         } else {
             const size_t sm1 = TcDims<1>::BYTES;
             AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm1));
-            grid_learned_tc_kernel<1><<<ctas, 256, sm1, st>>>(a, s->d_err);
+            grid_learned_tc_kernel<1><<<ctas, 128 * TcDims<1>::NWG, sm1, st>>>(a, s->d_err);
         }
         AW_CHECK_LAUNCH();
         unsigned int e = 0;
