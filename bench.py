@@ -484,6 +484,11 @@ def learned_section(ctx, dev, args):
     tabs2, _, _ = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=1e9)
     del tabs2
     ms_mlp = timed(run_learned, reps=1)
+    # the same inline evaluation on the older tensor-core engine (mma.sync), for comparison
+    aw.aw_surrogate_set_engine(sur, aw.AW_ENGINE_MMA_SYNC)
+    ms_mlp_sync = timed(run_learned, reps=1)
+    aw.aw_surrogate_set_engine(sur, aw.AW_ENGINE_TCGEN05)
+    run_learned()
     mlp_err, mlp_dr = err_vs_ref(g_le, exact)
     points = float(info.mean_taps) * info.nvalid
     mlp_flops = points * 2.0 * (5 * 128 + 3 * 128 * 128 + 128 * 32)
@@ -517,7 +522,10 @@ def learned_section(ctx, dev, args):
             "mvis_s_exact_tables": obs.nvis / (ms_ex / 1e3) / 1e6,
             "grid_ms_learned_with_rejection": ms_le, "grid_ms_learned_inline_all_planes": ms_mlp,
             "grid_ms_exact": ms_ex,
-            "inline_mlp_points": points, "inline_mlp_tflops_fp16_mma": mlp_flops / (ms_mlp / 1e3) / 1e12,
+            "inline_mlp_points": points, "inline_engine": "tcgen05 (FP16 operands, FP32 accumulators in TMEM)",
+            "inline_mlp_tflops": mlp_flops / (ms_mlp / 1e3) / 1e12,
+            "grid_ms_learned_inline_all_planes_mma_sync": ms_mlp_sync,
+            "inline_mlp_tflops_mma_sync": mlp_flops / (ms_mlp_sync / 1e3) / 1e12,
             "reference": "exact kernels at 128 w planes (4x finer); image errors over the inner half, Stokes I-V",
             "dirty_image_rel_err_exact_32_planes_vs_ref": ex_err, "dynamic_range_exact_32_planes": ex_dr,
             "dirty_image_rel_err_learned_with_rejection_vs_ref": img_err, "dynamic_range_learned_with_rejection": dr,
