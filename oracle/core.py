@@ -217,7 +217,7 @@ def invert4(A: np.ndarray) -> np.ndarray:
 # anti-aliasing function and the w term; Sec. 3.3 for the gridding copy)
 # ----------------------------------------------------------------------------
 
-ROLE_GRID, ROLE_DEGRID, ROLE_ADJOINT = 0, 1, 2
+ROLE_GRID, ROLE_DEGRID, ROLE_ADJOINT, ROLE_BEAM = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -237,6 +237,10 @@ class KernelSpec:
     d_yx: complex = 0.0
     eps: float = 0.2
     role: int = ROLE_GRID
+    # pointing of the antennas relative to the image phase centre (direction
+    # cosines): the beam is evaluated at (l - point_l, m - point_m)
+    point_l: float = 0.0
+    point_m: float = 0.0
 
     @property
     def npa(self) -> int:
@@ -280,8 +284,11 @@ def cell_functions(spec: KernelSpec, p: int, a: int, f: int) -> np.ndarray:
     grid:    f_{s,c} = psi psi * exp(+2 pi i w (n-1)) * ((M^S)'^-1 T)_{s,c}
     degrid:  f_{c,s} = psi psi * exp(-2 pi i w (n-1)) * (M T^-1)_{c,s}
     adjoint: f_{c,s} = conj(grid f_{s,c})
+    beam:    f_{s,c} = conj(degrid f_{c,s}): gridding weighted by the beam (the
+             exact adjoint of degridding; UV-domain mosaics, Sec. 2.2)
     npol == 1 has no A term: the Mueller factor is 1.
-    (M^S)' is M^S with its diagonal regularised by Eq. 6.
+    (M^S)' is M^S with its diagonal regularised by Eq. 6.  The beam is the
+    Jones matrix at (l - point_l, m - point_m).
     """
     M = spec.image_size(p)
     l1 = image_coords(spec, M)
@@ -296,14 +303,17 @@ def cell_functions(spec: KernelSpec, p: int, a: int, f: int) -> np.ndarray:
     wphase = np.exp(2j * math.pi * w * (n - 1.0))  # gridding sign
     role = spec.role
     if spec.npol == 1:
-        if role == ROLE_GRID:
+        if role in (ROLE_GRID, ROLE_BEAM):
             return (psi2 * wphase)[None]
         return np.conj(psi2 * wphase)[None]
-    J = jones(l, m, spec.fbin_freqs[f], spec.pa[a], spec.dish_d, spec.d_xy, spec.d_yx)
+    J = jones(l - spec.point_l, m - spec.point_m, spec.fbin_freqs[f], spec.pa[a], spec.dish_d, spec.d_xy,
+              spec.d_yx)
     Mu = mueller_from_jones(J)
-    if role == ROLE_DEGRID:
+    if role in (ROLE_DEGRID, ROLE_BEAM):
         A = Mu @ T_STOKES_TO_CORR                           # [M][M][c][s]
         fn = (psi2 * np.conj(wphase))[..., None, None] * A
+        if role == ROLE_BEAM:
+            fn = np.conj(np.swapaxes(fn, -1, -2))           # [s][c] = conj(degrid[c][s])
         return np.moveaxis(fn.reshape(M, M, 16), -1, 0)
     MS = mueller_stokes(Mu)
     MSr = MS.copy()
@@ -335,7 +345,7 @@ def synth_bin(spec: KernelSpec, b: int, offsets_y: Optional[Sequence[int]] = Non
     """Kernel table of bin b: [len(oy)][len(ox)][S][S][P] complex128.
 
     K(ky, kx) = (1/M^2) sum_{q,p} f[q][p] exp(sign 2 pi i (ky (q-M/2) + kx (p-M/2)) / (M OS))
-    with sign = -1 for the gridding role and +1 for degrid/adjoint: the DFT of
+    with sign = -1 for the gridding and beam roles and +1 for degrid/adjoint: the DFT of
     the zero-padded image function evaluated at the uv samples the table needs.
     The 1/M^2 (with psi(0) = 1) makes the untruncated zero-offset taper kernel
     sum to one over integer cells (Poisson summation of the M-point DFT).
@@ -349,7 +359,7 @@ def synth_bin(spec: KernelSpec, b: int, offsets_y: Optional[Sequence[int]] = Non
     OS = spec.OS
     oy = list(range(OS)) if offsets_y is None else list(offsets_y)
     ox = list(range(OS)) if offsets_x is None else list(offsets_x)
-    sign = -1.0 if spec.role == ROLE_GRID else 1.0
+    sign = -1.0 if spec.role in (ROLE_GRID, ROLE_BEAM) else 1.0
     fn = cell_functions(spec, p, a, f)                 # [P][M][M] (q = y, p = x)
     Ey = _dft_rows(M, OS, S, sign, oy)                 # [(oy, jy)][q]
     Ex = _dft_rows(M, OS, S, sign, ox)                 # [(ox, jx)][p]
@@ -545,6 +555,32 @@ def degrid(ks: KernelSet, co: Coords, G: np.ndarray) -> np.ndarray:
                        _ptr(co.bin), _ptr(co.flip), _ptr(co.valid), _ptr(tab), _ptr(ks.offsets),
                        _ptr(ks.bin_support), spec.OS, spec.N, _ptr(out))
     return out
+
+
+def frame_axes(ra0: float, dec0: float) -> np.ndarray:
+    """Rows: the unit vectors (east, north, towards the phase centre) of the
+    frame about (ra0, dec0), in equatorial coordinates."""
+    sa, ca, sd, cd = math.sin(ra0), math.cos(ra0), math.sin(dec0), math.cos(dec0)
+    return np.array([[-sa, ca, 0.0], [-sd * ca, -sd * sa, cd], [cd * ca, cd * sa, sd]])
+
+
+def phase_rotate(uvw: np.ndarray, row_of_vis: np.ndarray, chan_of_vis: np.ndarray, freq: np.ndarray,
+                 vis: np.ndarray, src_centre, dst_centre):
+    """Move visibilities from phase centre src_centre = (ra, dec) to dst_centre.
+
+    The baseline b (metres) is unchanged; its components in the frame of the new
+    centre are uvw' = B_dst B_src^T uvw.  With the degridding convention
+    V = sum I exp(-2 pi i (u l + v m + w (n - 1))) = exp(2 pi i w) sum I exp(-2 pi i b.s / lambda),
+    the visibility about the new centre is V' = V exp(2 pi i (w' - w) nu / c).
+    Returns (uvw' [nrow][3], vis' [nvis][npol])."""
+    R = frame_axes(*dst_centre) @ frame_axes(*src_centre).T
+    uvw = np.asarray(uvw, np.float64)
+    uvw2 = uvw @ R.T
+    dw = (uvw2[:, 2] - uvw[:, 2])[np.asarray(row_of_vis, np.int64)]
+    lam_inv = np.asarray(freq, np.float64)[np.asarray(chan_of_vis, np.int64)] / C_LIGHT
+    ph = np.exp(2j * math.pi * dw * lam_inv)
+    v = np.asarray(vis, np.complex128)
+    return uvw2, v * (ph[:, None] if v.ndim == 2 else ph)
 
 
 def uvw_lambda(uvw: np.ndarray, row_of_vis: np.ndarray, chan_of_vis: np.ndarray,
