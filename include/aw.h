@@ -51,6 +51,9 @@ extern "C" {
 #define AW_ROLE_GRID 0       /* uv transform of psi W ((M^S)'^-1 T): corr -> Stokes */
 #define AW_ROLE_DEGRID 1     /* uv transform of psi W* (M T^-1): Stokes -> corr     */
 #define AW_ROLE_ADJOINT 2    /* conjugate transpose of the GRID role               */
+#define AW_ROLE_BEAM 3       /* conjugate transpose of the DEGRID role: gridding
+                              * weighted by the beam (the exact adjoint of
+                              * degridding), for UV-domain mosaics (Sec. 2.2)      */
 
 #define AW_STORAGE_FP32 0    /* complex64 tables                                  */
 #define AW_STORAGE_BF16 1    /* complex as two bfloat16, FP32 arithmetic          */
@@ -88,6 +91,10 @@ typedef struct aw_kernel_spec {
     double eps;              /* Eq. 6 masking fraction (paper: typically 0.2)   */
     int32_t role;            /* AW_ROLE_*                                        */
     int32_t storage;         /* AW_STORAGE_*                                     */
+    double point_l, point_m; /* antenna pointing relative to the image phase
+                              * centre (direction cosines): the beam is evaluated
+                              * at (l - point_l, m - point_m); 0 for a single
+                              * pointing, the field offset in UV-domain mosaics   */
 } aw_kernel_spec;
 
 typedef struct aw_kernel_info {
@@ -495,6 +502,21 @@ int aw_reproject(aw_ctx *ctx, const float *src, const aw_sky_frame *src_frame, f
  */
 int aw_mosaic_combine(aw_ctx *ctx, const float *images, const float *beams, const float *gamma, int32_t nfield,
                       int32_t nplane, int32_t N, float *out, void *stream);
+
+/*
+ * aw_phase_rotate - move visibilities to a new phase centre: each field of a
+ * UV-domain mosaic (Sec. 2.2) is gridded about the mosaic's centre.  The
+ * baselines are unchanged; their components about the new centre are
+ * uvw' = B_to B_from^T uvw (B: rows east, north, centre of a frame), and with
+ * the degridding convention V = sum I exp(-2 pi i (u l + v m + w (n - 1))) the
+ * visibilities become V' = V exp(2 pi i (w' - w) nu / c).  Rotation and phase
+ * in FP64, the product in FP32.  vd: the observation (uvw metres, rows,
+ * channels, frequencies; device arrays); uvw_out: device f64 [nrow][3] or NULL
+ * (must not alias vd->uvw: the phases read the input uvw); vis, vis_out:
+ * device complex64 [nvis][npol] (may alias).  Centres (ra, dec) in radians.
+ */
+int aw_phase_rotate(aw_ctx *ctx, const aw_vis_desc *vd, double *uvw_out, const void *vis, void *vis_out, int32_t npol,
+                    double ra_from, double dec_from, double ra_to, double dec_to, void *stream);
 
 /* ---- cleaning: Cotton-Schwab major cycles, Hogbom minor cycle ---------------
  *

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libaw.so")
 
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ETIMEOUT, AW_EUNSUPPORTED, AW_EREJECTED = range(7)
-AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT = 0, 1, 2
+AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT, AW_ROLE_BEAM = 0, 1, 2, 3
 AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
 AW_GRID_TILES, AW_GRID_OFFSETS = 0, 1
 AW_INTERP_BILINEAR, AW_INTERP_CUBIC = 0, 1
@@ -30,7 +30,7 @@ class aw_kernel_spec(ctypes.Structure):
                 ("npa", c_i32), ("pa", ctypes.POINTER(c_dbl)), ("nfb", c_i32),
                 ("fbin_freqs", ctypes.POINTER(c_dbl)), ("dish_d", c_dbl),
                 ("d_xy", c_dbl * 2), ("d_yx", c_dbl * 2), ("eps", c_dbl), ("role", c_i32),
-                ("storage", c_i32)]
+                ("storage", c_i32), ("point_l", c_dbl), ("point_m", c_dbl)]
 
 
 class aw_kernel_info(ctypes.Structure):
@@ -112,6 +112,8 @@ SIGNATURES = {
     "aw_reproject": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(aw_sky_frame), c_p, ctypes.POINTER(aw_sky_frame),
                                     c_i32, c_i32, ctypes.c_float, c_p]),
     "aw_mosaic_combine": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_i32, c_i32, c_i32, c_p, c_p]),
+    "aw_phase_rotate": (ctypes.c_int, [c_p, ctypes.POINTER(aw_vis_desc), c_p, c_p, c_p, c_i32, c_dbl, c_dbl, c_dbl,
+                                       c_dbl, c_p]),
     "aw_degrid_subtract": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_psf_sidelobe": (ctypes.c_int, [c_p, c_p, c_i32, ctypes.POINTER(ctypes.c_float), c_p]),
     "aw_hogbom": (ctypes.c_int, [c_p, c_p, c_p, c_i32, c_i32, ctypes.c_float, ctypes.c_float, c_i32, c_i32,
@@ -238,7 +240,7 @@ def make_spec(N: int, dl: float, OS: int, W: float = 7.0, npol: int = 1, nw: int
               w_max: float = 0.0, supports: Sequence[int] = (7,), pa: Sequence[float] = (0.0,),
               fbin_freqs: Sequence[float] = (1.4e9,), dish_d: float = 12.0, d_xy: complex = 0j,
               d_yx: complex = 0j, eps: float = 0.2, role: int = AW_ROLE_GRID,
-              storage: int = AW_STORAGE_FP32):
+              storage: int = AW_STORAGE_FP32, point_l: float = 0.0, point_m: float = 0.0):
     """Build an aw_kernel_spec (returns (spec, keepalive))."""
     sup = (c_i32 * len(supports))(*[int(s) for s in supports])
     pa_arr = (c_dbl * len(pa))(*[float(x) for x in pa])
@@ -254,6 +256,7 @@ def make_spec(N: int, dl: float, OS: int, W: float = 7.0, npol: int = 1, nw: int
     s.d_xy[0], s.d_xy[1] = complex(d_xy).real, complex(d_xy).imag
     s.d_yx[0], s.d_yx[1] = complex(d_yx).real, complex(d_yx).imag
     s.eps, s.role, s.storage = float(eps), int(role), int(storage)
+    s.point_l, s.point_m = float(point_l), float(point_m)
     return s, (sup, pa_arr, fb_arr)
 
 
@@ -386,6 +389,14 @@ def aw_reproject(ctx: Handle, src, src_frame: aw_sky_frame, dst, dst_frame: aw_s
     nplane = int(src.shape[0])
     _check(load().aw_reproject(ctx.ptr, _ptr(src), ctypes.byref(src_frame), _ptr(dst), ctypes.byref(dst_frame),
                                nplane, int(interp), ctypes.c_float(fill), _stream(stream)), "aw_reproject")
+
+
+def aw_phase_rotate(ctx: Handle, vd: aw_vis_desc, uvw_out, vis, vis_out, src_centre, dst_centre, stream=None):
+    """uvw_out: CUDA float64 [nrow][3] or None; vis, vis_out: CUDA complex64 [nvis][npol]."""
+    npol = int(vis.shape[1]) if vis is not None and vis.dim() == 2 else 1
+    _check(load().aw_phase_rotate(ctx.ptr, ctypes.byref(vd), _ptr(uvw_out), _ptr(vis), _ptr(vis_out), npol,
+                                  float(src_centre[0]), float(src_centre[1]), float(dst_centre[0]),
+                                  float(dst_centre[1]), _stream(stream)), "aw_phase_rotate")
 
 
 def aw_mosaic_combine(ctx: Handle, images, beams, gamma, out, stream=None):

@@ -132,6 +132,35 @@ __global__ void combine_kernel(const float *images, const float *beams, const fl
     }
 }
 
+// uvw' = R uvw per row (FP64)
+__global__ void rotate_uvw_kernel(const double *uvw, double *out, int64_t nrow, double r0, double r1, double r2,
+                                  double r3, double r4, double r5, double r6, double r7, double r8) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrow; i += (int64_t)gridDim.x * blockDim.x) {
+        const double u = uvw[3 * i], v = uvw[3 * i + 1], w = uvw[3 * i + 2];
+        out[3 * i] = r0 * u + r1 * v + r2 * w;
+        out[3 * i + 1] = r3 * u + r4 * v + r5 * w;
+        out[3 * i + 2] = r6 * u + r7 * v + r8 * w;
+    }
+}
+
+// V' = V exp(2 pi i (w' - w) nu / c), the phase in FP64
+__global__ void rotate_vis_kernel(const double *uvw, const uint32_t *row, const uint16_t *chan, const double *freq,
+                                  int64_t nvis, int npol, const float2 *vin, float2 *vout, double r6, double r7,
+                                  double r8) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvis; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = row[i];
+        const double u = uvw[3 * r], v = uvw[3 * r + 1], w = uvw[3 * r + 2];
+        const double dw = (r6 * u + r7 * v + r8 * w) - w;
+        double sp, cp;
+        sincos(2.0 * M_PI * (dw * (freq[chan[i]] / AW_C_LIGHT)), &sp, &cp);
+        const float c = (float)cp, sn = (float)sp;
+        for (int k = 0; k < npol; ++k) {
+            const float2 a = vin[i * npol + k];
+            vout[i * npol + k] = make_float2(a.x * c - a.y * sn, a.x * sn + a.y * c);
+        }
+    }
+}
+
 int nblk(int64_t n, int t) {
     int64_t b = (n + t - 1) / t;
     if (b < 1) b = 1;
@@ -212,6 +241,44 @@ int aw_reproject(aw_ctx *ctx, const float *src, const aw_sky_frame *sf, float *d
     else
         reproject_kernel<AW_INTERP_BILINEAR><<<nblk(npix, 256), 256, 0, s>>>(a);
     AW_CHECK_LAUNCH();
+    return AW_OK;
+    MO_GUARD_END
+}
+
+int aw_phase_rotate(aw_ctx *ctx, const aw_vis_desc *vd, double *uvw_out, const void *vis, void *vis_out, int32_t npol,
+                    double ra_from, double dec_from, double ra_to, double dec_to, void *stream) {
+    MO_GUARD_BEGIN
+    if (!ctx || !vd) return aw_set_error(AW_EINVAL, "NULL argument");
+    if (npol != 1 && npol != 4) return aw_set_error(AW_EINVAL, "npol %d", npol);
+    if (vd->nvis < 0 || vd->nrow < 0) return aw_set_error(AW_EINVAL, "negative sizes");
+    if (vd->nvis > 0 && (!vd->uvw || !vd->row_of_vis || !vd->chan_of_vis || !vd->freq || !vis || !vis_out))
+        return aw_set_error(AW_EINVAL, "vis descriptor or buffers incomplete");
+    if (uvw_out && uvw_out == vd->uvw) return aw_set_error(AW_EINVAL, "uvw_out must not alias the input uvw");
+    if (!std::isfinite(ra_from) || !std::isfinite(dec_from) || !std::isfinite(ra_to) || !std::isfinite(dec_to))
+        return aw_set_error(AW_EINVAL, "phase centres must be finite");
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    double Bf[9], Bt[9], R[9];
+    frame_axes(ra_from, dec_from, Bf);
+    frame_axes(ra_to, dec_to, Bt);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += Bt[3 * i + k] * Bf[3 * j + k];
+            R[3 * i + j] = v;
+        }
+    cudaStream_t s = S_(stream);
+    if (vd->nvis > 0) {
+        rotate_vis_kernel<<<nblk(vd->nvis, 256), 256, 0, s>>>(vd->uvw, vd->row_of_vis, vd->chan_of_vis, vd->freq,
+                                                             vd->nvis, npol, reinterpret_cast<const float2 *>(vis),
+                                                             reinterpret_cast<float2 *>(vis_out), R[6], R[7], R[8]);
+        AW_CHECK_LAUNCH();
+    }
+    if (uvw_out && vd->nrow > 0) {
+        rotate_uvw_kernel<<<nblk(vd->nrow, 256), 256, 0, s>>>(vd->uvw, uvw_out, vd->nrow, R[0], R[1], R[2], R[3], R[4],
+                                                             R[5], R[6], R[7], R[8]);
+        AW_CHECK_LAUNCH();
+    }
     return AW_OK;
     MO_GUARD_END
 }

@@ -118,6 +118,7 @@ struct SynthParams {
     double dish;
     double dxy_r, dxy_i, dyx_r, dyx_i;
     double eps;
+    double point_l, point_m;      // antenna pointing relative to the phase centre
     const double *taper;          // [M], taper[0] = 0
     unsigned long long *bmax;     // [4] max |M^S_pp| as double bits
     cufftDoubleComplex *Z;        // [P][MO][MO]
@@ -147,6 +148,9 @@ __device__ __forceinline__ cd Tinv_cs(int c, int s) {
 
 // Mueller matrix M = J kron conj(J), J = E [[1, dxy], [dyx, 1]] R(chi).
 __device__ void mueller_at(const SynthParams &p, double l, double m, cd Mu[16]) {
+    // the beam is centred on the pointing
+    l -= p.point_l;
+    m -= p.point_m;
     const double r = sqrt(l * l + m * m);
     const double x = M_PI * p.dish * r / p.lambda;
     const double E = (x == 0.0) ? 1.0 : 2.0 * j1(x) / x;
@@ -258,20 +262,24 @@ __global__ void synth_cells_kernel(SynthParams p) {
         const size_t plane = (size_t)MO * MO;
         const size_t off = (size_t)qq * MO + pc;
         if (p.npol == 1) {
-            const cd f = (p.role == AW_ROLE_GRID) ? wg : cconj(wg);
+            const cd f = (p.role == AW_ROLE_GRID || p.role == AW_ROLE_BEAM) ? wg : cconj(wg);
             p.Z[off] = make_cuDoubleComplex(f.r, f.i);
             continue;
         }
         cd Mu[16];
         mueller_at(p, l, m, Mu);
-        if (p.role == AW_ROLE_DEGRID) {
+        if (p.role == AW_ROLE_DEGRID || p.role == AW_ROLE_BEAM) {
+            // degrid: [c][s] = W* (M T^-1)_{c,s}; beam: [s][c] = conj(degrid [c][s])
             const cd wd = cconj(wg);
             for (int c = 0; c < 4; ++c)
                 for (int s = 0; s < 4; ++s) {
                     cd acc = {0, 0};
                     for (int b = 0; b < 4; ++b) acc = cadd(acc, cmul(Mu[c * 4 + b], Tinv_cs(b, s)));
                     const cd f = cmul(wd, acc);
-                    p.Z[(size_t)(c * 4 + s) * plane + off] = make_cuDoubleComplex(f.r, f.i);
+                    if (p.role == AW_ROLE_DEGRID)
+                        p.Z[(size_t)(c * 4 + s) * plane + off] = make_cuDoubleComplex(f.r, f.i);
+                    else
+                        p.Z[(size_t)(s * 4 + c) * plane + off] = make_cuDoubleComplex(f.r, -f.i);
                 }
             continue;
         }
@@ -443,7 +451,10 @@ int aw_kernel_set_geometry(const aw_kernel_spec *spec, aw_kernel_set *ks) {
     if (spec->nw < 1 || spec->nw > 256) return aw_set_error(AW_EINVAL, "nw=%d out of [1, 256]", spec->nw);
     if (!spec->supports) return aw_set_error(AW_EINVAL, "supports is NULL");
     if (!(spec->dl > 0) || !(spec->W > 0)) return aw_set_error(AW_EINVAL, "dl and W must be positive");
-    if (spec->role < 0 || spec->role > 2) return aw_set_error(AW_EINVAL, "bad role %d", spec->role);
+    if (spec->role < 0 || spec->role > 3) return aw_set_error(AW_EINVAL, "bad role %d", spec->role);
+    if (!std::isfinite(spec->point_l) || !std::isfinite(spec->point_m) ||
+        spec->point_l * spec->point_l + spec->point_m * spec->point_m >= 1.0)
+        return aw_set_error(AW_EINVAL, "pointing (%g, %g) not on the visible hemisphere", spec->point_l, spec->point_m);
     if (spec->storage < 0 || spec->storage > 2) return aw_set_error(AW_EINVAL, "bad storage %d", spec->storage);
     const int npa = spec->npa < 1 ? 1 : spec->npa;
     const int nfb = spec->nfb < 1 ? 1 : spec->nfb;
@@ -566,9 +577,10 @@ int aw_synthesise(aw_ctx *ctx, aw_kernel_set *ks, cudaStream_t s) {
                 prm.lambda = AW_C_LIGHT / ks->fbin_freqs[f]; prm.dish = sp.dish_d;
                 prm.dxy_r = sp.d_xy[0]; prm.dxy_i = sp.d_xy[1]; prm.dyx_r = sp.d_yx[0]; prm.dyx_i = sp.d_yx[1];
                 prm.eps = sp.eps; prm.taper = d_taper; prm.bmax = d_bmax; prm.Z = Z;
+                prm.point_l = sp.point_l; prm.point_m = sp.point_m;
                 const size_t zbytes = (size_t)P * MO * MO * sizeof(cufftDoubleComplex);
                 e = cudaMemsetAsync(Z, 0, zbytes, s);
-                if (e == cudaSuccess && sp.npol == 4 && sp.role != AW_ROLE_DEGRID) {
+                if (e == cudaSuccess && sp.npol == 4 && (sp.role == AW_ROLE_GRID || sp.role == AW_ROLE_ADJOINT)) {
                     e = cudaMemsetAsync(d_bmax, 0, 4 * sizeof(unsigned long long), s);
                     if (e == cudaSuccess) {
                         synth_bmax_kernel<<<blocks_for((int64_t)M * M, 128, 1024), 128, 0, s>>>(prm);
@@ -580,7 +592,7 @@ int aw_synthesise(aw_ctx *ctx, aw_kernel_set *ks, cudaStream_t s) {
                     e = cudaGetLastError();
                 }
                 if (e != cudaSuccess) { rc = aw_set_error(AW_ECUDA, "synthesis kernels: %s", cudaGetErrorString(e)); break; }
-                const int dir = (sp.role == AW_ROLE_GRID) ? CUFFT_FORWARD : CUFFT_INVERSE;
+                const int dir = (sp.role == AW_ROLE_GRID || sp.role == AW_ROLE_BEAM) ? CUFFT_FORWARD : CUFFT_INVERSE;
                 if (cufftExecZ2Z(plan, Z, Z, dir) != CUFFT_SUCCESS) { rc = aw_set_error(AW_ECUDA, "cufftExecZ2Z failed"); break; }
                 const double scale = (double)ks->scale / ((double)M * M);
                 const int64_t n = (int64_t)OS * OS * S * S * P;
