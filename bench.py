@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
-    ap.add_argument("--no-mosaic", action="store_true", help="skip the image-domain mosaic measurement")
+    ap.add_argument("--no-mosaic", action="store_true", help="skip the mosaic measurements")
+    ap.add_argument("--uvmosaic-fraction", type=float, default=0.1,
+                    help="fraction of each mosaic field's visibilities in the UV/image-domain comparison")
     ap.add_argument("--clean-major", type=int, default=3, help="major cycles of the cleaning measurement")
     ap.add_argument("--learned-steps", type=int, default=8000)
     ap.add_argument("--learned-fraction", type=float, default=0.1,
@@ -375,6 +377,117 @@ def mosaic_section(ctx, dev, args, stream):
             "gpix_per_s_fields_to_mosaic": out_px_fwd / (res["forward"] / 1e3) / 1e9,
             "gpix_per_s_mosaic_to_fields": out_px_bwd / (res["backward"] / 1e3) / 1e9,
             "note": "a pixel = all 4 Stokes planes; FP64 position (3x3 rotation) and floor, FP32 weights and 4x4 interpolation"}
+
+
+def uvmosaic_section(ctx, dev, args, stream):
+    """Image-domain against UV-domain mosaicing of the 7 hexagonal fields of the
+    mosaic workload (Sec. 2.2), on the same visibilities (a seeded fraction of
+    each field's 10M).  Image domain: each field gridded at its own phase centre
+    on 2048^2 x 4 (3 deg; GRID kernels, 4 w planes, supports 8-32), imaged,
+    reprojected to a 4096^2 common frame (Keys cubic) and combined with Eq. 1.
+    UV domain: each field phase-rotated to the mosaic centre and gridded onto
+    one 4096^2 x 4 grid (6 deg) with beam-weighted kernels centred on its
+    pointing; the larger field doubles the uv extent of the beam and w kernels,
+    so the supports are doubled (16-64); one FFT, then gamma.  Kernel
+    synthesis, plans and beams are prepared before the timed regions."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import synthetic as sy
+    g = sy.grid_geometry(5)
+    Nf, dl = g["N"], g["dl"]
+    Nm = 2 * Nf
+    dec0 = math.radians(sy.DEC_DEG)
+    ra0 = 1.0
+    centre = (ra0, dec0)
+    fr_m = aw.sky_frame(ra0, dec0, dl, Nm)
+    offs = sy.mosaic_offsets()
+    fields = []
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(91)
+    nvis_total = 0
+    for f, (ex_deg, no_deg) in enumerate(offs):
+        ob = sy.observation(5, field=f, vis_fraction=args.uvmosaic_fraction)
+        pc = (ra0 + math.radians(ex_deg) / math.cos(dec0), dec0 + math.radians(no_deg))
+        # pointing of field f in the common frame
+        B0 = np.array([[-math.sin(ra0), math.cos(ra0), 0.0],
+                       [-math.sin(dec0) * math.cos(ra0), -math.sin(dec0) * math.sin(ra0), math.cos(dec0)]])
+        sv = np.array([math.cos(pc[1]) * math.cos(pc[0]), math.cos(pc[1]) * math.sin(pc[0]), math.sin(pc[1])])
+        lp, mp = B0 @ sv
+        base = dict(OS=8, W=7.0, npol=4, nw=4, w_max=ob.w_max, pa=list(ob.pa_centres), fbin_freqs=list(ob.fbin_freqs),
+                    dish_d=12.0, d_xy=0.01 * np.exp(0.4j), d_yx=0.01 * np.exp(-1.3j), eps=0.2)
+        kimg = aw.aw_make_kernels(ctx, N=Nf, dl=dl, supports=[8, 16, 24, 32], **base)
+        kuv = aw.aw_make_kernels(ctx, N=Nm, dl=dl, supports=[16, 32, 48, 64], role=aw.AW_ROLE_BEAM,
+                                 point_l=float(lp), point_m=float(mp), **base)
+        vd, keep = aw.device_observation(ob, dev)
+        plan_img = aw.aw_plan_create(ctx, vd, kimg)
+        vis = torch.randn((ob.nvis, 4), dtype=torch.complex64, device=dev, generator=gen)
+        vrot = torch.empty_like(vis)
+        uvw_rot = torch.empty((ob.uvw.shape[0], 3), dtype=torch.float64, device=dev)
+        aw.aw_phase_rotate(ctx, vd, uvw_rot, vis, vrot, pc, centre)
+        vd_uv, keep_uv = aw.device_observation(ob, dev)
+        vd_uv.uvw = uvw_rot.data_ptr()
+        plan_uv = aw.aw_plan_create(ctx, vd_uv, kuv)
+        fields.append(dict(frame=aw.sky_frame(pc[0], pc[1], dl, Nf), kimg=kimg, kuv=kuv, plan_img=plan_img,
+                           plan_uv=plan_uv, vd=vd, keep=(keep, keep_uv, uvw_rot), vis=vis, vrot=vrot,
+                           pc=pc, nvis=ob.nvis))
+        nvis_total += ob.nvis
+    # Airy power beams of the pointings on the common frame (flat-sky offsets), gamma
+    q = (torch.arange(Nm, device=dev, dtype=torch.float64) - Nm // 2) * dl
+    lam = 299792458.0 / 1.35e9
+    from scipy.special import j1
+    beams = torch.empty((len(offs), Nm, Nm), dtype=torch.float32, device=dev)
+    for f, (ex_deg, no_deg) in enumerate(offs):
+        r = torch.hypot(q[None, :] - math.radians(ex_deg), q[:, None] - math.radians(no_deg))
+        x = (math.pi * 12.0 / lam * r).cpu().numpy()
+        e = np.where(x == 0, 1.0, 2.0 * j1(np.where(x == 0, 1.0, x)) / np.where(x == 0, 1.0, x))
+        beams[f] = torch.as_tensor((e * e).astype(np.float32), device=dev)
+    gam = torch.empty((Nm, Nm), dtype=torch.float32, device=dev)
+    aw.mosaic_gamma(ctx, beams, 0.2, gam)
+    grid_f = torch.zeros((4, Nf, Nf), dtype=torch.complex64, device=dev)
+    img_f = torch.empty((4, Nf, Nf), dtype=torch.float32, device=dev)
+    onm = torch.empty((len(offs), 4, Nm, Nm), dtype=torch.float32, device=dev)
+    mosaic = torch.empty((4, Nm, Nm), dtype=torch.float32, device=dev)
+    grid_m = torch.zeros((4, Nm, Nm), dtype=torch.complex64, device=dev)
+    img_m = torch.empty((4, Nm, Nm), dtype=torch.float32, device=dev)
+    ones = torch.ones((1, Nm, Nm), dtype=torch.float32, device=dev)
+
+    def image_domain():
+        for f, fd in enumerate(fields):
+            grid_f.zero_()
+            aw.aw_grid_batched(ctx, fd["plan_img"], fd["kimg"], fd["vis"], None, grid_f)
+            aw.aw_fft_to_image(ctx, fd["kimg"], grid_f, float(fd["nvis"]), img_f)
+            aw.aw_reproject(ctx, img_f, fd["frame"], onm[f], fr_m, aw.AW_INTERP_CUBIC)
+        aw.aw_mosaic_combine(ctx, onm, beams, gam, mosaic)
+
+    def uv_domain():
+        grid_m.zero_()
+        for fd in fields:
+            aw.aw_phase_rotate(ctx, fd["vd"], None, fd["vis"], fd["vrot"], fd["pc"], centre)
+            aw.aw_grid_batched(ctx, fd["plan_uv"], fd["kuv"], fd["vrot"], None, grid_m)
+        aw.aw_fft_to_image(ctx, fields[0]["kuv"], grid_m, float(nvis_total), img_m)
+        aw.aw_mosaic_combine(ctx, img_m[None], ones, gam, mosaic)
+
+    res = {}
+    for name, fn in (("image_domain", image_domain), ("uv_domain", uv_domain)):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / 3
+    out = {"workload": "7 hexagonal fields, %d visibilities in all; image domain 2048^2 x 4 per field + "
+                       "reprojection to 4096^2; UV domain one 4096^2 x 4 grid" % nvis_total,
+           "ms_image_domain": res["image_domain"], "ms_uv_domain": res["uv_domain"],
+           "mvis_s_image_domain": nvis_total / (res["image_domain"] / 1e3) / 1e6,
+           "mvis_s_uv_domain": nvis_total / (res["uv_domain"] / 1e3) / 1e6,
+           "table_bytes_image_domain": int(sum(aw.aw_kernel_set_info(fd["kimg"]).bytes for fd in fields)),
+           "table_bytes_uv_domain": int(sum(aw.aw_kernel_set_info(fd["kuv"]).bytes for fd in fields))}
+    del fields, beams, gam, onm, mosaic, grid_m, img_m, grid_f, img_f, ones
+    torch.cuda.empty_cache()
+    return out
 
 
 def learned_section(ctx, dev, args):
@@ -757,6 +870,7 @@ def run_ours(args, rank, world, dist):
     mosaic = None
     if not args.no_mosaic and not args.subset:
         mosaic = mosaic_section(ctx, dev, args, stream)
+        mosaic["uv_vs_image_domain"] = uvmosaic_section(ctx, dev, args, stream)
     learned = None
     if not args.no_learned:
         # free the FP32 workload before the learned comparison
