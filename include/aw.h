@@ -68,9 +68,12 @@ typedef struct aw_surrogate aw_surrogate;
 /*
  * Bins: w plane p (nw planes linear in |w|, centres (p + 1/2) w_max / nw;
  * nw = 1 switches the w term off), parallactic-angle bin a, beam-frequency
- * bin f; bin index (p * npa + a) * nfb + f.  Sec. 3.2 of the paper averages
- * beams over channel ranges ("for performance reasons"); these bins are that
- * averaging.
+ * bin f, and with ntype >= 2 the baseline class k = ti * ntype + tj; bin index
+ * ((k * nw + p) * npa + a) * nfb + f.  Sec. 3.2 of the paper averages beams
+ * over channel ranges and baselines ("for performance reasons"); these bins
+ * are that averaging, and the baseline classes undo the baseline part of it.
+ * A visibility flipped to w >= 0 (V -> P conj V) is the reversed baseline and
+ * takes class tj * ntype + ti.
  */
 typedef struct aw_kernel_spec {
     int32_t N;               /* grid side                                        */
@@ -95,6 +98,13 @@ typedef struct aw_kernel_spec {
                               * centre (direction cosines): the beam is evaluated
                               * at (l - point_l, m - point_m); 0 for a single
                               * pointing, the field offset in UV-domain mosaics   */
+    int32_t ntype;           /* antenna types with their own leakage, 0..16; 0 or
+                              * 1: every antenna has d_xy, d_yx (baseline-averaged
+                              * Mueller kernels, Sec. 3.2).  >= 2: per-baseline
+                              * kernels, one class per ordered type pair (ti, tj)
+                              * with M = J_ti kron conj(J_tj)                     */
+    const double *type_leak; /* host [ntype][4]: d_xy (re, im), d_yx (re, im) per
+                              * type; NULL if ntype <= 1                          */
 } aw_kernel_spec;
 
 typedef struct aw_kernel_info {
@@ -121,6 +131,11 @@ typedef struct aw_vis_desc {
     const uint8_t *pa_bin;      /* device [nrow] or NULL (all 0)                 */
     const uint8_t *fbin;        /* device [nchan] or NULL (all 0)                */
     const uint8_t *flags;       /* device [nvis] or NULL; nonzero = flagged      */
+    const uint8_t *row_types;   /* device [nrow][2] or NULL: types of the row's two
+                                 * antennas, in the order of the baseline the uvw
+                                 * belongs to (read only by kernel sets with
+                                 * ntype >= 2; NULL means type 0 for both; values
+                                 * >= ntype count as ntype - 1)                   */
 } aw_vis_desc;
 
 typedef struct aw_tune {
@@ -233,7 +248,8 @@ int aw_kernel_set_destroy(aw_kernel_set *kset);
  * cells, position in tile) and cut into work items of at most tune->chunk.
  * The plan depends on the kernel set only through N, OS, the bins and their
  * supports; any set with the same geometry may be used with it.
- * tune == NULL uses tile 32, chunk 256.  Synchronises `stream`.
+ * tune == NULL uses the last aw_autotune result of this context (its cache),
+ * or tile 32, chunk 256 if the context has none.  Synchronises `stream`.
  */
 int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset,
                    const aw_tune *tune, aw_plan **out, void *stream);
@@ -299,7 +315,8 @@ int aw_grid_batched(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kset, const
  * aw_autotune - time aw_grid_batched over candidate (tile, chunk,
  * ctas_per_sm) of the TILES schedule and two super-tile sizes of the OFFSETS
  * schedule on the given visibilities (pass a subsample to keep it short) and
- * return the fastest in *out.  Uses a scratch grid it allocates.
+ * return the fastest in *out; it is also kept in the context as the tune
+ * aw_plan_create uses when given NULL.  Uses a scratch grid it allocates.
  * Synchronises `stream`.
  */
 int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset, aw_tune *out,
@@ -381,7 +398,9 @@ int aw_surrogate_forward(aw_ctx *ctx, aw_surrogate *sur, const float *X, int32_t
 int aw_surrogate_loss_grad(aw_ctx *ctx, aw_surrogate *sur, const float *X, const float *T, int32_t B,
                            double *loss, float *grad, void *stream);
 /* Train on random (bin, fine offset, tap) points of `exact` (its role and
- * npol must match the surrogate).  Synchronises `stream`. */
+ * npol must match the surrogate).  The network has no baseline-class input:
+ * a set with ntype >= 2 returns AW_EUNSUPPORTED here, in aw_surrogate_tables
+ * and in aw_grid_learned.  Synchronises `stream`. */
 int aw_surrogate_train(aw_ctx *ctx, aw_surrogate *sur, const aw_kernel_set *exact, const aw_train_cfg *cfg,
                        aw_train_report *report, void *stream);
 /*

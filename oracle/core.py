@@ -158,11 +158,15 @@ def jones(l: np.ndarray, m: np.ndarray, freq_hz: float, chi: float, dish_d: floa
     return E[..., None, None] * DR
 
 
-def mueller_from_jones(J: np.ndarray) -> np.ndarray:
-    """M = J kron conj(J) (Eq. 2-3 text; the conjugate on the second factor
-    is the reading for correlations <e_a e_b*>).  Shape (..., 4, 4)."""
+def mueller_from_jones(J: np.ndarray, J2: Optional[np.ndarray] = None) -> np.ndarray:
+    """M = J kron conj(J2) (Eq. 2-3 text; the conjugate on the second factor
+    is the reading for correlations <e_a e_b*>): the Mueller matrix of a
+    baseline whose first antenna has Jones matrix J and second J2 (J2 = J when
+    omitted: identical antennas).  Shape (..., 4, 4)."""
+    if J2 is None:
+        J2 = J
     a = J[..., :, None, :, None]
-    b = np.conj(J)[..., None, :, None, :]
+    b = np.conj(J2)[..., None, :, None, :]
     M = a * b  # (..., 2, 2, 2, 2) indices (a, b, c, d)
     return M.reshape(J.shape[:-2] + (4, 4))
 
@@ -241,6 +245,11 @@ class KernelSpec:
     # cosines): the beam is evaluated at (l - point_l, m - point_m)
     point_l: float = 0.0
     point_m: float = 0.0
+    # per-baseline Mueller kernels: leakage (d_xy, d_yx) of each antenna type;
+    # with two or more types every ordered type pair (ti, tj) is a baseline
+    # class with its own kernels, M = J_ti kron conj(J_tj).  Empty: every
+    # antenna has (d_xy, d_yx) and the kernels are baseline-averaged.
+    type_leak: Sequence = ()
 
     @property
     def npa(self) -> int:
@@ -251,8 +260,36 @@ class KernelSpec:
         return len(self.fbin_freqs)
 
     @property
+    def ntype(self) -> int:
+        return len(self.type_leak)
+
+    @property
+    def nclass(self) -> int:
+        return self.ntype * self.ntype if self.ntype >= 2 else 1
+
+    @property
     def nbins(self) -> int:
-        return self.nw * self.npa * self.nfb
+        return self.nclass * self.nw * self.npa * self.nfb
+
+    def decode_bin(self, b: int):
+        """(class k, w plane p, PA bin a, frequency bin f) of bin
+        b = ((k nw + p) npa + a) nfb + f."""
+        f = b % self.nfb
+        a = (b // self.nfb) % self.npa
+        p = (b // (self.nfb * self.npa)) % self.nw
+        k = b // (self.nfb * self.npa * self.nw)
+        return k, p, a, f
+
+    def plane_of(self, b):
+        return (np.asarray(b) // (self.npa * self.nfb)) % self.nw
+
+    def leakages(self, k: int):
+        """((d_xy, d_yx) of the first antenna, (d_xy, d_yx) of the second) of
+        baseline class k = ti * ntype + tj."""
+        if self.nclass == 1:
+            return (self.d_xy, self.d_yx), (self.d_xy, self.d_yx)
+        ti, tj = divmod(k, self.ntype)
+        return tuple(self.type_leak[ti]), tuple(self.type_leak[tj])
 
     def w_centre(self, p: int) -> float:
         if self.nw <= 1:
@@ -278,7 +315,7 @@ def image_coords(spec: KernelSpec, M: int):
     return l1
 
 
-def cell_functions(spec: KernelSpec, p: int, a: int, f: int) -> np.ndarray:
+def cell_functions(spec: KernelSpec, p: int, a: int, f: int, k: int = 0) -> np.ndarray:
     """Image-domain functions [P][M][M] whose uv transforms are the kernels.
 
     grid:    f_{s,c} = psi psi * exp(+2 pi i w (n-1)) * ((M^S)'^-1 T)_{s,c}
@@ -288,7 +325,8 @@ def cell_functions(spec: KernelSpec, p: int, a: int, f: int) -> np.ndarray:
              exact adjoint of degridding; UV-domain mosaics, Sec. 2.2)
     npol == 1 has no A term: the Mueller factor is 1.
     (M^S)' is M^S with its diagonal regularised by Eq. 6.  The beam is the
-    Jones matrix at (l - point_l, m - point_m).
+    Jones matrix at (l - point_l, m - point_m); M = J_i kron conj(J_j) with the
+    two antennas' leakages of baseline class k.
     """
     M = spec.image_size(p)
     l1 = image_coords(spec, M)
@@ -306,9 +344,10 @@ def cell_functions(spec: KernelSpec, p: int, a: int, f: int) -> np.ndarray:
         if role in (ROLE_GRID, ROLE_BEAM):
             return (psi2 * wphase)[None]
         return np.conj(psi2 * wphase)[None]
-    J = jones(l - spec.point_l, m - spec.point_m, spec.fbin_freqs[f], spec.pa[a], spec.dish_d, spec.d_xy,
-              spec.d_yx)
-    Mu = mueller_from_jones(J)
+    (dxy_i, dyx_i), (dxy_j, dyx_j) = spec.leakages(k)
+    Ji = jones(l - spec.point_l, m - spec.point_m, spec.fbin_freqs[f], spec.pa[a], spec.dish_d, dxy_i, dyx_i)
+    Jj = jones(l - spec.point_l, m - spec.point_m, spec.fbin_freqs[f], spec.pa[a], spec.dish_d, dxy_j, dyx_j)
+    Mu = mueller_from_jones(Ji, Jj)
     if role in (ROLE_DEGRID, ROLE_BEAM):
         A = Mu @ T_STOKES_TO_CORR                           # [M][M][c][s]
         fn = (psi2 * np.conj(wphase))[..., None, None] * A
@@ -350,17 +389,14 @@ def synth_bin(spec: KernelSpec, b: int, offsets_y: Optional[Sequence[int]] = Non
     The 1/M^2 (with psi(0) = 1) makes the untruncated zero-offset taper kernel
     sum to one over integer cells (Poisson summation of the M-point DFT).
     """
-    nfb, npa = spec.nfb, spec.npa
-    p = b // (npa * nfb)
-    a = (b // nfb) % npa
-    f = b % nfb
+    k, p, a, f = spec.decode_bin(b)
     S = int(spec.supports[p])
     M = spec.image_size(p)
     OS = spec.OS
     oy = list(range(OS)) if offsets_y is None else list(offsets_y)
     ox = list(range(OS)) if offsets_x is None else list(offsets_x)
     sign = -1.0 if spec.role in (ROLE_GRID, ROLE_BEAM) else 1.0
-    fn = cell_functions(spec, p, a, f)                 # [P][M][M] (q = y, p = x)
+    fn = cell_functions(spec, p, a, f, k)              # [P][M][M] (q = y, p = x)
     Ey = _dft_rows(M, OS, S, sign, oy)                 # [(oy, jy)][q]
     Ex = _dft_rows(M, OS, S, sign, ox)                 # [(ox, jx)][p]
     P = fn.shape[0]
@@ -392,8 +428,7 @@ def make_kernels(spec: KernelSpec, bins: Optional[Sequence[int]] = None) -> Kern
     pos = 0
     P = spec.npol * spec.npol
     for b in range(nb):
-        p = b // (spec.npa * spec.nfb)
-        S = int(spec.supports[p])
+        S = int(spec.supports[spec.plane_of(b)])
         sup[b] = S
         offs[b] = pos
         if b in want:
@@ -508,8 +543,15 @@ class Coords:
 
 def coords(spec: KernelSpec, uvw: np.ndarray, row_of_vis: np.ndarray, chan_of_vis: np.ndarray,
            freq: np.ndarray, pa_bin: Optional[np.ndarray] = None,
-           fbin: Optional[np.ndarray] = None, flags: Optional[np.ndarray] = None) -> Coords:
-    """Per-visibility integer coordinates (see oracle_coords in aw_oracle.c)."""
+           fbin: Optional[np.ndarray] = None, flags: Optional[np.ndarray] = None,
+           row_types: Optional[np.ndarray] = None) -> Coords:
+    """Per-visibility integer coordinates (see oracle_coords in aw_oracle.c).
+
+    With per-baseline kernels (spec.ntype >= 2) row_types [nrow][2] gives the
+    types of each row's two antennas (None: type 0 for both; types past the
+    last count as the last).  A visibility flipped to w >= 0 is the reversed
+    baseline, V_ji = P conj(V_ij) at -uvw, so its class takes the two types in
+    swapped order."""
     nvis = int(row_of_vis.shape[0])
     uvw = np.ascontiguousarray(uvw, dtype=np.float64)
     row = np.ascontiguousarray(row_of_vis, dtype=np.uint32)
@@ -523,7 +565,13 @@ def coords(spec: KernelSpec, uvw: np.ndarray, row_of_vis: np.ndarray, chan_of_vi
     _c().oracle_coords(nvis, _ptr(uvw), _ptr(row), _ptr(chan), _ptr(freq), _ptr(pa_bin),
                        _ptr(fbin), _ptr(flags), spec.N, spec.dl, spec.OS, spec.nw, spec.w_max,
                        spec.npa, spec.nfb, _ptr(sup), *[_ptr(a) for a in out])
-    return Coords(*out)
+    co = Coords(*out)
+    if spec.nclass > 1 and row_types is not None:
+        rt = np.minimum(np.asarray(row_types, np.int64).reshape(-1, 2), spec.ntype - 1)[row]
+        ti = np.where(co.flip == 1, rt[:, 1], rt[:, 0])
+        tj = np.where(co.flip == 1, rt[:, 0], rt[:, 1])
+        co.bin = (co.bin + (ti * spec.ntype + tj) * (spec.nw * spec.npa * spec.nfb)).astype(np.int32)
+    return co
 
 
 def grid(ks: KernelSet, co: Coords, vis: np.ndarray, weight: Optional[np.ndarray] = None):
@@ -627,7 +675,7 @@ def degrid_sampled(spec: KernelSpec, G: np.ndarray, co: Coords, idx) -> np.ndarr
         if not co.valid[k]:
             continue
         b = int(co.bin[k])
-        S = int(spec.supports[b // (spec.npa * spec.nfb)])
+        S = int(spec.supports[spec.plane_of(b)])
         K = synth_bin(spec, b, offsets_y=[int(co.fy[k])], offsets_x=[int(co.fx[k])])[0, 0]   # [S][S][P]
         x0, y0 = int(co.x0[k]), int(co.y0[k])
         win = np.asarray(G[:, y0:y0 + S, x0:x0 + S], dtype=np.complex128)                  # [s][S][S]

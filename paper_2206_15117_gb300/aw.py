@@ -30,7 +30,8 @@ class aw_kernel_spec(ctypes.Structure):
                 ("npa", c_i32), ("pa", ctypes.POINTER(c_dbl)), ("nfb", c_i32),
                 ("fbin_freqs", ctypes.POINTER(c_dbl)), ("dish_d", c_dbl),
                 ("d_xy", c_dbl * 2), ("d_yx", c_dbl * 2), ("eps", c_dbl), ("role", c_i32),
-                ("storage", c_i32), ("point_l", c_dbl), ("point_m", c_dbl)]
+                ("storage", c_i32), ("point_l", c_dbl), ("point_m", c_dbl), ("ntype", c_i32),
+                ("type_leak", ctypes.POINTER(c_dbl))]
 
 
 class aw_kernel_info(ctypes.Structure):
@@ -42,7 +43,7 @@ class aw_kernel_info(ctypes.Structure):
 class aw_vis_desc(ctypes.Structure):
     _fields_ = [("nvis", c_i64), ("nrow", c_i64), ("nchan", c_i32), ("uvw", c_p),
                 ("row_of_vis", c_p), ("chan_of_vis", c_p), ("freq", c_p), ("pa_bin", c_p),
-                ("fbin", c_p), ("flags", c_p)]
+                ("fbin", c_p), ("flags", c_p), ("row_types", c_p)]
 
 
 class aw_tune(ctypes.Structure):
@@ -240,8 +241,10 @@ def make_spec(N: int, dl: float, OS: int, W: float = 7.0, npol: int = 1, nw: int
               w_max: float = 0.0, supports: Sequence[int] = (7,), pa: Sequence[float] = (0.0,),
               fbin_freqs: Sequence[float] = (1.4e9,), dish_d: float = 12.0, d_xy: complex = 0j,
               d_yx: complex = 0j, eps: float = 0.2, role: int = AW_ROLE_GRID,
-              storage: int = AW_STORAGE_FP32, point_l: float = 0.0, point_m: float = 0.0):
-    """Build an aw_kernel_spec (returns (spec, keepalive))."""
+              storage: int = AW_STORAGE_FP32, point_l: float = 0.0, point_m: float = 0.0,
+              type_leak: Optional[Sequence] = None):
+    """Build an aw_kernel_spec (returns (spec, keepalive)).  type_leak: per
+    antenna type a (d_xy, d_yx) pair of complex leakages (per-baseline kernels)."""
     sup = (c_i32 * len(supports))(*[int(s) for s in supports])
     pa_arr = (c_dbl * len(pa))(*[float(x) for x in pa])
     fb_arr = (c_dbl * len(fbin_freqs))(*[float(x) for x in fbin_freqs])
@@ -257,7 +260,15 @@ def make_spec(N: int, dl: float, OS: int, W: float = 7.0, npol: int = 1, nw: int
     s.d_yx[0], s.d_yx[1] = complex(d_yx).real, complex(d_yx).imag
     s.eps, s.role, s.storage = float(eps), int(role), int(storage)
     s.point_l, s.point_m = float(point_l), float(point_m)
-    return s, (sup, pa_arr, fb_arr)
+    tl = None
+    if type_leak:
+        vals = []
+        for dxy_t, dyx_t in type_leak:
+            vals += [complex(dxy_t).real, complex(dxy_t).imag, complex(dyx_t).real, complex(dyx_t).imag]
+        tl = (c_dbl * len(vals))(*vals)
+        s.ntype = len(type_leak)
+        s.type_leak = ctypes.cast(tl, ctypes.POINTER(c_dbl))
+    return s, (sup, pa_arr, fb_arr, tl)
 
 
 def aw_make_kernels(ctx: Handle, stream=None, **spec_kw) -> Handle:
@@ -291,14 +302,16 @@ def aw_kernel_set_destroy(kset: Handle):
     kset.close()
 
 
-def vis_desc(uvw, row_of_vis, chan_of_vis, freq, pa_bin=None, fbin=None, flags=None) -> aw_vis_desc:
+def vis_desc(uvw, row_of_vis, chan_of_vis, freq, pa_bin=None, fbin=None, flags=None,
+             row_types=None) -> aw_vis_desc:
     d = aw_vis_desc()
     d.nvis = int(row_of_vis.numel())
     d.nrow = int(uvw.shape[0])
     d.nchan = int(freq.numel())
     d.uvw, d.row_of_vis, d.chan_of_vis, d.freq = _ptr(uvw), _ptr(row_of_vis), _ptr(chan_of_vis), _ptr(freq)
     d.pa_bin, d.fbin, d.flags = _ptr(pa_bin), _ptr(fbin), _ptr(flags)
-    d._keep = (uvw, row_of_vis, chan_of_vis, freq, pa_bin, fbin, flags)
+    d.row_types = _ptr(row_types)
+    d._keep = (uvw, row_of_vis, chan_of_vis, freq, pa_bin, fbin, flags, row_types)
     return d
 
 
@@ -441,11 +454,12 @@ def aw_clean(ctx: Handle, plan: Handle, kgrid: Handle, kdegrid: Handle, vis, wei
     return rep
 
 
-def device_observation(ob, device="cuda:0", flags=None):
+def device_observation(ob, device="cuda:0", flags=None, row_types=None):
     """Copy a synthetic Observation's arrays to the device and describe them.
 
     Returns (aw_vis_desc, dict of tensors).  Row and channel indices are
-    passed as int32 / int16 bit patterns of the uint32 / uint16 ABI types."""
+    passed as int32 / int16 bit patterns of the uint32 / uint16 ABI types.
+    row_types: optional host uint8 [nrow][2] antenna types of each row."""
     import numpy as np
     import torch
 
@@ -460,9 +474,10 @@ def device_observation(ob, device="cuda:0", flags=None):
         "pa_bin": t(ob.pa_bin.astype(np.uint8), torch.uint8),
         "fbin": t(ob.fbin.astype(np.uint8), torch.uint8),
         "flags": t(None if flags is None else flags.astype(np.uint8), torch.uint8),
+        "row_types": t(None if row_types is None else np.asarray(row_types, np.uint8).reshape(-1, 2), torch.uint8),
     }
     d = vis_desc(tens["uvw"], tens["row"], tens["chan"], tens["freq"], tens["pa_bin"], tens["fbin"],
-                 tens["flags"])
+                 tens["flags"], tens["row_types"])
     return d, tens
 
 

@@ -218,6 +218,7 @@ int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kse
     if (rc) return rc;
     aw_plan *p = new aw_plan();
     p->device = ctx->device;
+    if (!tune && ctx->has_tune) tune = &ctx->tune_cache;
     rc = aw_plan_build(ctx, vis, kset, tune, p, S_(stream));
     if (rc != AW_OK) { free_plan(p); return rc; }
     *out = p;
@@ -269,7 +270,7 @@ int aw_plan_order(const aw_plan *p, uint32_t *perm, void *stream) {
 
 static int check_pair(const aw_plan *p, const aw_kernel_set *k) {
     if (!p || !k) return aw_set_error(AW_EINVAL, "plan/kset is NULL");
-    if (p->N != k->spec.N || p->OS != k->spec.OS || p->npol != k->spec.npol || p->nbins != k->nbins ||
+    if (p->N != k->spec.N || p->OS != k->spec.OS || p->npol != k->spec.npol || p->nbins != k->nbins || p->ntype != k->ntype ||
         p->bin_support != k->bin_support)
         return aw_set_error(AW_EINVAL, "kernel set geometry does not match the plan");
     return AW_OK;
@@ -451,6 +452,8 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
     cudaFree(v);
     if (rc) return rc;
     *out = bt;
+    ctx->tune_cache = bt;
+    ctx->has_tune = true;
     return AW_OK;
     AW_GUARD_END
 }

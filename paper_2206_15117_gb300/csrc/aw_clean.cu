@@ -367,7 +367,7 @@ struct DevMem {
 
 int check_plan_kset(const aw_plan *p, const aw_kernel_set *k) {
     if (!p || !k) return aw_set_error(AW_EINVAL, "plan/kset is NULL");
-    if (p->N != k->spec.N || p->OS != k->spec.OS || p->npol != k->spec.npol || p->nbins != k->nbins ||
+    if (p->N != k->spec.N || p->OS != k->spec.OS || p->npol != k->spec.npol || p->nbins != k->nbins || p->ntype != k->ntype ||
         p->bin_support != k->bin_support)
         return aw_set_error(AW_EINVAL, "kernel set geometry does not match the plan");
     return AW_OK;

@@ -50,6 +50,9 @@ struct aw_ctx {
     std::map<std::pair<int, double>, float *> gridcorr;
     // small device scratch: [0] reduction word for mosaic_gamma
     unsigned int *d_scratch = nullptr;
+    // last aw_autotune result (used by aw_plan_create when given no tune)
+    bool has_tune = false;
+    aw_tune tune_cache{};
 };
 
 struct aw_kernel_set {
@@ -57,6 +60,9 @@ struct aw_kernel_set {
     aw_kernel_spec spec{};          // copied; pointer members re-pointed to the vectors
     std::vector<int32_t> supports;  // per w plane
     std::vector<double> pa, fbin_freqs;
+    std::vector<double> type_leak;  // [ntype][4] per-type leakage (ntype >= 2)
+    int ntype = 1;                  // antenna types; baseline classes = ntype^2 if >= 2
+    int nclass = 1;
     int nbins = 0;
     int P = 1;                      // npol * npol
     int max_support = 0;
@@ -91,6 +97,7 @@ struct aw_plan {
     int device = 0;
     int64_t nvis = 0, nvalid = 0, n_outside = 0, n_flagged = 0, nitems = 0;
     int N = 0, OS = 0, npol = 1, nbins = 0, nw = 1, npa = 1, nfb = 1;
+    int ntype = 1;                  // baseline classes are ntype^2 when ntype >= 2
     aw_tune tune{};
     double mean_taps = 0;
     aw_rec *d_rec = nullptr;        // [nvis] sorted (valid first) by (bin, tile, position)

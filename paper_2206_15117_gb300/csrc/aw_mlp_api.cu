@@ -146,6 +146,7 @@ int aw_surrogate_train(aw_ctx *ctx, aw_surrogate *s, const aw_kernel_set *exact,
     if (!ctx || !s || !exact || !cfg) return aw_set_error(AW_EINVAL, "NULL argument");
     if (cfg->steps < 1 || cfg->batch < 64 || cfg->batch > (1 << 20))
         return aw_set_error(AW_EINVAL, "steps %d / batch %d out of range", cfg->steps, cfg->batch);
+    if (exact->nclass > 1) return aw_set_error(AW_EUNSUPPORTED, "the surrogate has no baseline-class input");
     int rc = set_dev(s->device);
     if (rc) return rc;
     return aw_sur_train(s, exact, cfg, report, S_(stream));
@@ -158,6 +159,7 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *s, const aw_kernel_set *exact
     if (!ctx || !s || !exact || !out) return aw_set_error(AW_EINVAL, "NULL argument");
     *out = nullptr;
     if (exact->P * 2 != s->sizes.back()) return aw_set_error(AW_EINVAL, "surrogate / kernel set npol differ");
+    if (exact->nclass > 1) return aw_set_error(AW_EUNSUPPORTED, "the surrogate has no baseline-class input");
     if (storage != exact->spec.storage)
         return aw_set_error(AW_EUNSUPPORTED, "surrogate tables use the exact set's storage (%d), asked %d",
                             exact->spec.storage, storage);
@@ -201,6 +203,7 @@ extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, c
     if (p->N != fallback->spec.N || p->OS != fallback->spec.OS || p->nbins != fallback->nbins ||
         p->bin_support != fallback->bin_support || p->npol != fallback->spec.npol)
         return aw_set_error(AW_EINVAL, "fallback kernel set geometry does not match the plan");
+    if (fallback->nclass > 1) return aw_set_error(AW_EUNSUPPORTED, "the surrogate has no baseline-class input");
     int rc = set_dev(s->device);
     if (rc) return rc;
     cudaStream_t st = S_(stream);

@@ -18,7 +18,8 @@ struct CoordArgs {
     const uint8_t *pa_bin;
     const uint8_t *fbin;
     const uint8_t *flags;
-    int N, OS, nw, npa, nfb;
+    const uint8_t *row_types;  // [nrow][2] or NULL
+    int N, OS, nw, npa, nfb, ntype;
     double uscale, half, winv;
     const int32_t *support;  // per w plane
     int tile, tbits, ntx, nty;
@@ -57,7 +58,15 @@ __device__ __forceinline__ CoordOut coord_of(const CoordArgs &a, int64_t k) {
     }
     const int pa = a.pa_bin ? (int)a.pa_bin[r] : 0;
     const int fb = a.fbin ? (int)a.fbin[c] : 0;
-    o.bin = (wp * a.npa + min(pa, a.npa - 1)) * a.nfb + min(fb, a.nfb - 1);
+    int cls = 0;
+    if (a.ntype >= 2 && a.row_types) {
+        // the flipped sample is the reversed baseline: its class swaps the types
+        int ti = min((int)a.row_types[2 * (int64_t)r], a.ntype - 1);
+        int tj = min((int)a.row_types[2 * (int64_t)r + 1], a.ntype - 1);
+        if (o.flip) { const int t = ti; ti = tj; tj = t; }
+        cls = ti * a.ntype + tj;
+    }
+    o.bin = ((cls * a.nw + wp) * a.npa + min(pa, a.npa - 1)) * a.nfb + min(fb, a.nfb - 1);
     const int S = a.support[wp];
     o.S = S;
     const long long rho = (long long)(S - 2) * a.OS / 2;
@@ -321,11 +330,13 @@ int fill_coord_args(const aw_vis_desc *vis, const aw_kernel_set *ks, int tile, C
     a.pa_bin = vis->pa_bin;
     a.fbin = vis->fbin;
     a.flags = vis->flags;
+    a.row_types = vis->row_types;
     a.N = sp.N;
     a.OS = sp.OS;
     a.nw = sp.nw;
     a.npa = sp.npa;
     a.nfb = sp.nfb;
+    a.ntype = ks->ntype;
     a.uscale = (double)sp.N * sp.dl * (double)sp.OS;
     a.half = (double)(sp.N / 2) * (double)sp.OS;
     a.winv = (sp.nw > 1 && sp.w_max > 0.0) ? (double)sp.nw / sp.w_max : 0.0;
@@ -427,6 +438,7 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     plan->nw = sp.nw;
     plan->npa = sp.npa;
     plan->nfb = sp.nfb;
+    plan->ntype = ks->ntype;
     plan->vis = *vis;
     // per-plane supports first (the coordinate step indexes by w plane), then per bin
     std::vector<int32_t> sup(ks->supports.begin(), ks->supports.end());
@@ -534,11 +546,13 @@ int aw_plan_coords_impl(const aw_plan *plan, const aw_kernel_set *ks_unused, int
     a.pa_bin = vis->pa_bin;
     a.fbin = vis->fbin;
     a.flags = vis->flags;
+    a.row_types = vis->row_types;
     a.N = plan->N;
     a.OS = plan->OS;
     a.nw = plan->nw;
     a.npa = plan->npa;
     a.nfb = plan->nfb;
+    a.ntype = plan->ntype;
     a.uscale = plan->uscale;
     a.half = plan->half;
     a.winv = plan->winv;

@@ -116,7 +116,8 @@ struct SynthParams {
     double chi;         // parallactic angle
     double lambda;      // wavelength of the beam-frequency bin
     double dish;
-    double dxy_r, dxy_i, dyx_r, dyx_i;
+    double dxy_r, dxy_i, dyx_r, dyx_i;     // leakage of the first antenna of the baseline
+    double dxy2_r, dxy2_i, dyx2_r, dyx2_i; // and of the second
     double eps;
     double point_l, point_m;      // antenna pointing relative to the phase centre
     const double *taper;          // [M], taper[0] = 0
@@ -146,7 +147,17 @@ __device__ __forceinline__ cd Tinv_cs(int c, int s) {
     }
 }
 
-// Mueller matrix M = J kron conj(J), J = E [[1, dxy], [dyx, 1]] R(chi).
+// Jones matrix E [[1, dxy], [dyx, 1]] R(chi), R = [[c, -s], [s, c]].
+__device__ __forceinline__ void jones_at(double E, double sc, double cc, double dxy_r, double dxy_i, double dyx_r,
+                                         double dyx_i, cd J[2][2]) {
+    J[0][0] = {E * (cc + dxy_r * sc), E * (dxy_i * sc)};
+    J[0][1] = {E * (-sc + dxy_r * cc), E * (dxy_i * cc)};
+    J[1][0] = {E * (dyx_r * cc + sc), E * (dyx_i * cc)};
+    J[1][1] = {E * (-dyx_r * sc + cc), E * (-dyx_i * sc)};
+}
+
+// Mueller matrix of a baseline (i, j): M = J_i kron conj(J_j) (Sec. 2.1);
+// J_i = J_j for baseline-averaged kernels.
 __device__ void mueller_at(const SynthParams &p, double l, double m, cd Mu[16]) {
     // the beam is centred on the pointing
     l -= p.point_l;
@@ -156,19 +167,14 @@ __device__ void mueller_at(const SynthParams &p, double l, double m, cd Mu[16]) 
     const double E = (x == 0.0) ? 1.0 : 2.0 * j1(x) / x;
     double sc, cc;
     sincos(p.chi, &sc, &cc);
-    // D R with D = [[1, dxy], [dyx, 1]], R = [[c, -s], [s, c]]
-    cd J[2][2];
-    J[0][0] = {cc + p.dxy_r * sc, p.dxy_i * sc};
-    J[0][1] = {-sc + p.dxy_r * cc, p.dxy_i * cc};
-    J[1][0] = {p.dyx_r * cc + sc, p.dyx_i * cc};
-    J[1][1] = {-p.dyx_r * sc + cc, -p.dyx_i * sc};
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) J[a][b] = cscale(J[a][b], E);
+    cd Ji[2][2], Jj[2][2];
+    jones_at(E, sc, cc, p.dxy_r, p.dxy_i, p.dyx_r, p.dyx_i, Ji);
+    jones_at(E, sc, cc, p.dxy2_r, p.dxy2_i, p.dyx2_r, p.dyx2_i, Jj);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c)
                 for (int d = 0; d < 2; ++d)
-                    Mu[(2 * a + b) * 4 + (2 * c + d)] = cmul(J[a][c], cconj(J[b][d]));
+                    Mu[(2 * a + b) * 4 + (2 * c + d)] = cmul(Ji[a][c], cconj(Jj[b][d]));
 }
 
 __device__ void stokes_mueller(const cd Mu[16], cd MS[16]) {
@@ -460,7 +466,21 @@ int aw_kernel_set_geometry(const aw_kernel_spec *spec, aw_kernel_set *ks) {
     const int nfb = spec->nfb < 1 ? 1 : spec->nfb;
     if (spec->npol == 4 && ((spec->npa >= 1 && !spec->pa) || (spec->nfb >= 1 && !spec->fbin_freqs)))
         return aw_set_error(AW_EINVAL, "pa / fbin_freqs arrays are NULL");
-    if (spec->nw * npa * nfb > 65535) return aw_set_error(AW_EINVAL, "too many bins");
+    const int ntype = spec->ntype < 1 ? 1 : spec->ntype;
+    if (ntype > 16) return aw_set_error(AW_EINVAL, "ntype=%d out of [0, 16]", spec->ntype);
+    if (ntype >= 2 && spec->npol != 4) return aw_set_error(AW_EINVAL, "per-baseline kernels need npol = 4");
+    if (ntype >= 2 && !spec->type_leak) return aw_set_error(AW_EINVAL, "type_leak is NULL with ntype=%d", ntype);
+    const int nclass = ntype >= 2 ? ntype * ntype : 1;
+    if ((int64_t)nclass * spec->nw * npa * nfb > 65535) return aw_set_error(AW_EINVAL, "too many bins");
+    ks->ntype = ntype;
+    ks->nclass = nclass;
+    if (ntype >= 2) {
+        ks->type_leak.assign(spec->type_leak, spec->type_leak + 4 * ntype);
+        for (double d : ks->type_leak)
+            if (!std::isfinite(d)) return aw_set_error(AW_EINVAL, "type_leak holds a non-finite value");
+    } else {
+        ks->type_leak.clear();
+    }
     ks->supports.assign(spec->supports, spec->supports + spec->nw);
     for (int s : ks->supports) {
         if (s < 2 || s > 128) return aw_set_error(AW_EINVAL, "support %d out of [2, 128]", s);
@@ -482,14 +502,16 @@ int aw_kernel_set_geometry(const aw_kernel_spec *spec, aw_kernel_set *ks) {
     ks->spec.supports = ks->supports.data();
     ks->spec.pa = ks->pa.data();
     ks->spec.fbin_freqs = ks->fbin_freqs.data();
+    ks->spec.ntype = ntype;
+    ks->spec.type_leak = ks->type_leak.empty() ? nullptr : ks->type_leak.data();
     ks->P = spec->npol * spec->npol;
-    ks->nbins = spec->nw * npa * nfb;
+    ks->nbins = nclass * spec->nw * npa * nfb;
     ks->bin_support.resize(ks->nbins);
     ks->bin_offset.resize(ks->nbins);
     int64_t pos = 0;
     ks->max_support = 0;
     for (int b = 0; b < ks->nbins; ++b) {
-        const int p = b / (npa * nfb);
+        const int p = (b / (npa * nfb)) % spec->nw;
         const int S = ks->supports[p];
         ks->bin_support[b] = S;
         ks->bin_offset[b] = pos;
@@ -568,14 +590,24 @@ int aw_synthesise(aw_ctx *ctx, aw_kernel_set *ks, cudaStream_t s) {
         if (rc != AW_OK) break;
         if (cufftSetStream(plan, s) != CUFFT_SUCCESS) { rc = aw_set_error(AW_ECUDA, "cufftSetStream"); break; }
         const double w = sp.nw > 1 ? (p + 0.5) * sp.w_max / sp.nw : 0.0;
+        for (int k = 0; k < ks->nclass && rc == AW_OK; ++k)
         for (int a = 0; a < npa && rc == AW_OK; ++a)
             for (int f = 0; f < nfb && rc == AW_OK; ++f) {
-                const int b = (p * npa + a) * nfb + f;
+                const int b = ((k * sp.nw + p) * npa + a) * nfb + f;
                 SynthParams prm;
                 prm.M = M; prm.MO = MO; prm.S = S; prm.OS = OS; prm.P = P; prm.npol = sp.npol;
                 prm.role = sp.role; prm.F = F; prm.w = w; prm.chi = ks->pa[a];
                 prm.lambda = AW_C_LIGHT / ks->fbin_freqs[f]; prm.dish = sp.dish_d;
-                prm.dxy_r = sp.d_xy[0]; prm.dxy_i = sp.d_xy[1]; prm.dyx_r = sp.d_yx[0]; prm.dyx_i = sp.d_yx[1];
+                if (ks->nclass > 1) {
+                    // class k = ti * ntype + tj: baseline between antennas of types ti and tj
+                    const double *li = &ks->type_leak[4 * (k / ks->ntype)];
+                    const double *lj = &ks->type_leak[4 * (k % ks->ntype)];
+                    prm.dxy_r = li[0]; prm.dxy_i = li[1]; prm.dyx_r = li[2]; prm.dyx_i = li[3];
+                    prm.dxy2_r = lj[0]; prm.dxy2_i = lj[1]; prm.dyx2_r = lj[2]; prm.dyx2_i = lj[3];
+                } else {
+                    prm.dxy_r = sp.d_xy[0]; prm.dxy_i = sp.d_xy[1]; prm.dyx_r = sp.d_yx[0]; prm.dyx_i = sp.d_yx[1];
+                    prm.dxy2_r = prm.dxy_r; prm.dxy2_i = prm.dxy_i; prm.dyx2_r = prm.dyx_r; prm.dyx2_i = prm.dyx_i;
+                }
                 prm.eps = sp.eps; prm.taper = d_taper; prm.bmax = d_bmax; prm.Z = Z;
                 prm.point_l = sp.point_l; prm.point_m = sp.point_m;
                 const size_t zbytes = (size_t)P * MO * MO * sizeof(cufftDoubleComplex);

@@ -258,6 +258,15 @@ def small_observation(n_ant: int = 8, radius_m: float = 40.0, n_t: int = 8,
                        sources=np.zeros((0, 3)), params={"n_t": n_t})
 
 
+def row_antenna_types(n_ant: int, nrow: int, ant_type: np.ndarray) -> np.ndarray:
+    """uint8 [nrow][2]: the types of the two antennas (i < j) of each row, for
+    rows ordered time-major over the baselines of triu_indices(n_ant, 1)."""
+    i, j = np.triu_indices(n_ant, k=1)
+    bl = np.arange(nrow) % i.size
+    t = np.asarray(ant_type, np.uint8)
+    return np.stack([t[i[bl]], t[j[bl]]], axis=1)
+
+
 def random_grid(npol: int, N: int, seed: int = BASE_SEED + 11, scale: float = 1.0) -> np.ndarray:
     """A complex64 uv grid [npol][N][N] of Gaussian values (a model grid)."""
     rng = np.random.default_rng(seed)

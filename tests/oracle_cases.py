@@ -21,7 +21,7 @@ def quantised_uvw(spec, co):
     """Visibility coordinates after the method's own quantisation: the
     oversampled uv position it was gridded at and the centre of its w plane."""
     du = 1.0 / (spec.N * spec.dl)
-    p = co.bin // (spec.npa * spec.nfb)
+    p = spec.plane_of(co.bin)
     rho = (np.asarray(spec.supports)[p] - 2) * spec.OS // 2
     u = ((co.x0 * spec.OS + rho + co.fx) / spec.OS - spec.N // 2) * du
     v = ((co.y0 * spec.OS + rho + co.fy) / spec.OS - spec.N // 2) * du

@@ -46,7 +46,7 @@ def test_struct_sizes_match_header_layout(lib):
     # natural C layout on LP64: checked against the field order of the header
     assert ctypes.sizeof(aw.aw_tune) == 20
     assert ctypes.sizeof(aw.aw_stats) == 40
-    assert ctypes.sizeof(aw.aw_vis_desc) == 8 * 3 + 7 * 8
+    assert ctypes.sizeof(aw.aw_vis_desc) == 8 * 3 + 8 * 8
     assert ctypes.sizeof(aw.aw_plan_info) == 5 * 8 + 8 + 8 + 8
 
 

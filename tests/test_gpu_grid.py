@@ -240,3 +240,7 @@ def test_autotune_returns_a_valid_schedule(ctx):
     assert t.tile in (16, 32, 64) and t.chunk in (128, 256, 512)
     if t.grid_mode == aw.AW_GRID_OFFSETS:
         assert t.dg_tile in (256, 1024)
+    # the context keeps the result for plans made without a tune
+    vd2, _keep2 = aw.device_observation(ob)
+    info = aw.aw_plan_query(aw.aw_plan_create(ctx, vd2, kg))
+    assert (info.tile, info.chunk) == (t.tile, t.chunk)
