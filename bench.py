@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
     ap.add_argument("--no-mosaic", action="store_true", help="skip the mosaic measurements")
+    ap.add_argument("--no-baselines", action="store_true", help="skip the per-baseline kernel measurement")
     ap.add_argument("--uvmosaic-fraction", type=float, default=0.1,
                     help="fraction of each mosaic field's visibilities in the UV/image-domain comparison")
     ap.add_argument("--clean-major", type=int, default=3, help="major cycles of the cleaning measurement")
@@ -377,6 +378,59 @@ def mosaic_section(ctx, dev, args, stream):
             "gpix_per_s_fields_to_mosaic": out_px_fwd / (res["forward"] / 1e3) / 1e9,
             "gpix_per_s_mosaic_to_fields": out_px_bwd / (res["backward"] / 1e3) / 1e9,
             "note": "a pixel = all 4 Stokes planes; FP64 position (3x3 rotation) and floor, FP32 weights and 4x4 interpolation"}
+
+
+def baselines_section(ctx, dev, ob, kw, tune, vis, model, grid, vis_out, stream, averaged):
+    """Per-baseline Mueller kernels on the bench workload: the 36 antennas in
+    two types (two dish generations) with their own leakage terms, so 4
+    baseline classes with their own kernels, M = J_ti kron conj(J_tj), instead
+    of the baseline-averaged set.  Same visibilities, schedule and supports;
+    4x the kernel tables.  Timed: aw_grid_batched and aw_degrid as in the
+    main step."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import synthetic as sy
+    rng = np.random.default_rng(sy.BASE_SEED + 400)
+    ant_type = np.zeros(36, np.uint8)
+    ant_type[rng.permutation(36)[:18]] = 1
+    type_leak = [(0.01 * np.exp(0.4j), 0.01 * np.exp(-1.3j)), (0.015 * np.exp(-0.7j), 0.012 * np.exp(2.1j))]
+    rt = sy.row_antenna_types(36, ob.uvw.shape[0], ant_type)
+    t0 = time.perf_counter()
+    kg = aw.aw_make_kernels(ctx, **kw, type_leak=type_leak, role=aw.AW_ROLE_GRID)
+    kd = aw.aw_make_kernels(ctx, **kw, type_leak=type_leak, role=aw.AW_ROLE_DEGRID)
+    t_synth = time.perf_counter() - t0
+    vd, keep = aw.device_observation(ob, dev, row_types=rt)
+    t0 = time.perf_counter()
+    plan = aw.aw_plan_create(ctx, vd, kg, tune=tune)
+    t_plan = time.perf_counter() - t0
+    info = aw.aw_kernel_set_info(kg)
+
+    def step(ev=None):
+        grid.zero_()
+        if ev: ev[0].record(stream)
+        aw.aw_grid_batched(ctx, plan, kg, vis, None, grid)
+        if ev: ev[1].record(stream)
+        aw.aw_degrid(ctx, plan, kd, model, vis_out)
+        if ev: ev[2].record(stream)
+
+    step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(3)]
+    for e in evs:
+        step(e)
+    torch.cuda.synchronize()
+    gm = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    dm = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    nvis = int(ob.nvis)
+    out = {"workload": "bench workload with 2 antenna types (18 + 18 antennas): 4 baseline classes x 1024 bins, "
+                       "FP32 tables",
+           "classes": 4, "nbins": int(info.nbins), "table_bytes_per_set": int(info.bytes),
+           "grid_ms": gm, "degrid_ms": dm, "mvis_s": nvis / ((gm + dm) / 1e3) / 1e6,
+           "vs_baseline_averaged": (averaged["grid_ms"] + averaged["degrid_ms"]) / (gm + dm),
+           "once_per_dataset_s": {"kernel_synthesis_grid_and_degrid": t_synth, "plan_sort": t_plan}}
+    del kg, kd, plan, vd, keep
+    torch.cuda.empty_cache()
+    return out
 
 
 def uvmosaic_section(ctx, dev, args, stream):
@@ -871,6 +925,9 @@ def run_ours(args, rank, world, dist):
     if not args.no_mosaic and not args.subset:
         mosaic = mosaic_section(ctx, dev, args, stream)
         mosaic["uv_vs_image_domain"] = uvmosaic_section(ctx, dev, args, stream)
+    baselines = None
+    if not args.no_baselines and not args.subset:
+        baselines = baselines_section(ctx, dev, ob, kw, tune, vis, model, grid, vis_out, stream, variants["fp32"])
     learned = None
     if not args.no_learned:
         # free the FP32 workload before the learned comparison
@@ -900,7 +957,7 @@ def run_ours(args, rank, world, dist):
                 "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm,
                          "dg_tile": tune.dg_tile or 1024, "degrid_items": info.nitems_degrid,
                          "grid_schedule": ["tiles", "offsets"][tune.grid_mode]},
-                "clean": clean, "mosaic": mosaic, "learned": learned}
+                "clean": clean, "mosaic": mosaic, "per_baseline_kernels": baselines, "learned": learned}
         print(json.dumps(line), flush=True)
     return 0
 

@@ -142,3 +142,39 @@ def test_gridding_role_inverts_each_class_mueller_matrix():
         fo = oc.cell_functions(d, 0, 0, 0, 1 if k != 1 else 2).reshape(4, 4, M, M)
         wrong = np.einsum("scyx,ctyx->styx", fg, fo)[:, :, c, c]
         assert np.abs(wrong - eye).max() > 1e-2
+
+
+def test_per_channel_kernels_remove_the_frequency_averaging():
+    # one beam-frequency bin per channel: degridding equals the direct Mueller
+    # sum with each visibility's beam at its own channel frequency; the single
+    # band-averaged bin does not
+    ob, base = small_case(npol=4, W=9.0, S=16)
+    per_chan = oc.KernelSpec(**{**base, "fbin_freqs": tuple(ob.freq)}, role=oc.ROLE_DEGRID)
+    averaged = oc.KernelSpec(**base, role=oc.ROLE_DEGRID)
+    fbin = np.arange(ob.freq.size, dtype=np.uint8)
+    co = oc.coords(per_chan, ob.uvw, ob.row_of_vis, ob.chan_of_vis, ob.freq, fbin=fbin)
+    co_avg = oc.coords(averaged, ob.uvw, ob.row_of_vis, ob.chan_of_vis, ob.freq)
+    N, dl = per_chan.N, per_chan.dl
+    rng = np.random.default_rng(6)
+    qx = rng.integers(N // 2 - 20, N // 2 + 20, 4)
+    qy = rng.integers(N // 2 - 20, N // 2 + 20, 4)
+    lm = oc.pixel_lm(N, dl, qx, qy)
+    stokes = np.stack([rng.uniform(0.5, 1, 4), rng.uniform(-0.2, 0.2, 4),
+                       rng.uniform(-0.2, 0.2, 4), rng.uniform(-0.02, 0.02, 4)], 1)
+    uq = quantised_uvw(per_chan, co)
+    u_own = np.where(co.flip[:, None] == 1, -uq, uq)
+    Vobs = np.zeros((ob.nvis, 4), np.complex128)
+    for c, nu in enumerate(ob.freq):
+        sel = ob.chan_of_vis == c
+        J = oc.jones(lm[:, 0], lm[:, 1], nu, per_chan.pa[0], per_chan.dish_d, per_chan.d_xy, per_chan.d_yx)
+        bright = np.einsum("pcs,ps->pc", oc.mueller_from_jones(J) @ oc.T_STOKES_TO_CORR, stokes)
+        for k in range(4):
+            Vobs[sel, k] = oc.dft_predict(u_own[sel], lm, bright[:, k])
+    model = np.zeros((4, N, N))
+    for s in range(4):
+        np.add.at(model[s], (qy, qx), stokes[:, s])
+    G = oc.image_to_grid(model, per_chan.W)
+    err = np.abs(oc.degrid(oc.make_kernels(per_chan), co, G) - Vobs).max()
+    err_avg = np.abs(oc.degrid(oc.make_kernels(averaged), co_avg, G) - Vobs).max()
+    assert err < 1e-5 * np.abs(Vobs).max(), err
+    assert err_avg > 20 * err, (err, err_avg)
