@@ -446,6 +446,24 @@ int aw_grid_learned(aw_ctx *ctx, const aw_plan *plan, aw_surrogate *sur, const a
 enum { AW_ENGINE_MMA_SYNC = 0, AW_ENGINE_TCGEN05 = 1 };
 int aw_surrogate_set_engine(aw_surrogate *sur, int32_t engine);
 
+/*
+ * aw_surrogate_save - write the surrogate to the file `path` (created or
+ * truncated): its configuration, FP32 parameters, the per-w-plane rejection
+ * of the last aw_surrogate_tables call and the engine.  Every field is
+ * little-endian with no padding, after the 8-byte magic "AWSURR01", and the
+ * file ends with an FNV-1a 64 checksum of the bytes before it; the layout is
+ * the same on every host.  Adam moments are not saved.  Synchronises the
+ * device.  AW_EINVAL if the file cannot be written.
+ *
+ * aw_surrogate_load - create a surrogate on ctx's device from such a file
+ * (*out, freed with aw_surrogate_destroy).  Training continues from the
+ * loaded parameters with fresh Adam moments.  AW_EINVAL (and *out = NULL) if
+ * the file is missing, truncated, has trailing bytes, a bad magic or
+ * checksum, or a parameter count that does not match its configuration.
+ */
+int aw_surrogate_save(const aw_surrogate *sur, const char *path);
+int aw_surrogate_load(aw_ctx *ctx, const char *path, aw_surrogate **out);
+
 /* ---- mosaic weighting (Sec. 2.2, Eq. 1) ------------------------------------- */
 
 /*

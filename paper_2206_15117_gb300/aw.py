@@ -110,6 +110,8 @@ SIGNATURES = {
     "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_set_engine": (ctypes.c_int, [c_p, c_i32]),
+    "aw_surrogate_save": (ctypes.c_int, [c_p, ctypes.c_char_p]),
+    "aw_surrogate_load": (ctypes.c_int, [c_p, ctypes.c_char_p, ctypes.POINTER(c_p)]),
     "aw_reproject": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(aw_sky_frame), c_p, ctypes.POINTER(aw_sky_frame),
                                     c_i32, c_i32, ctypes.c_float, c_p]),
     "aw_mosaic_combine": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_i32, c_i32, c_i32, c_p, c_p]),
@@ -554,6 +556,16 @@ def aw_surrogate_tables(ctx: Handle, sur: Handle, exact: Handle, reject_rel: flo
 
 def aw_surrogate_set_engine(sur: Handle, engine: int):
     _check(load().aw_surrogate_set_engine(sur.ptr, int(engine)), "aw_surrogate_set_engine")
+
+
+def aw_surrogate_save(sur: Handle, path: str):
+    _check(load().aw_surrogate_save(sur.ptr, os.fsencode(path)), "aw_surrogate_save")
+
+
+def aw_surrogate_load(ctx: Handle, path: str) -> Handle:
+    out = c_p()
+    _check(load().aw_surrogate_load(ctx.ptr, os.fsencode(path), ctypes.byref(out)), "aw_surrogate_load")
+    return Handle(out, "aw_surrogate_destroy")
 
 
 def aw_grid_learned(ctx: Handle, plan: Handle, sur: Handle, fallback: Handle, vis, weight, grid,

@@ -94,3 +94,40 @@ def test_training_learns_the_kernels_and_rejects_per_plane(ctx):
     # what the network buys: its parameters against the tables it replaces
     nbytes_net = aw.aw_surrogate_nparams(sur) * 2          # FP16 weights
     assert nbytes_net < aw.aw_kernel_set_info(exact).bytes
+
+
+def test_save_and_load_round_trip(ctx, tmp_path):
+    # parameters, configuration, per-plane rejection and engine survive a file round trip bit-exactly
+    from paper_2206_15117_gb300 import aw
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=32, n_hidden=4, omega0=30.0, seed=11, D=1.5,
+                                 norm_supports=[16, 24, 32], w_max=500.0, f_c=1.3e9, f_h=0.1e9,
+                                 chi_c=0.2, chi_h=1.1, out_scale=0.03)
+    rng = np.random.default_rng(12)
+    p = (rng.standard_normal(aw.aw_surrogate_nparams(sur)) * 0.1).astype(np.float32)
+    aw.aw_surrogate_set_params(sur, p)
+    aw.aw_surrogate_set_engine(sur, aw.AW_ENGINE_MMA_SYNC)
+    path = str(tmp_path / "sur.bin")
+    aw.aw_surrogate_save(sur, path)
+    back = aw.aw_surrogate_load(ctx, path)
+    np.testing.assert_array_equal(aw.aw_surrogate_get_params(back), p)
+    X = torch.as_tensor(rng.uniform(-1, 1, (257, 5)).astype(np.float32), device="cuda")
+    Y0 = torch.empty((257, 32), dtype=torch.float32, device="cuda")
+    Y1 = torch.empty_like(Y0)
+    aw.aw_surrogate_forward(ctx, sur, X, Y0)
+    aw.aw_surrogate_forward(ctx, back, X, Y1)
+    torch.cuda.synchronize()
+    assert torch.equal(Y0, Y1)
+    # a second save of the loaded surrogate gives the same bytes
+    path2 = str(tmp_path / "sur2.bin")
+    aw.aw_surrogate_save(back, path2)
+    raw = open(path, "rb").read()
+    assert raw == open(path2, "rb").read()
+    assert raw[:8] == b"AWSURR01"
+    # damaged files are refused
+    bad = tmp_path / "bad.bin"
+    for blob in (raw[:-9], raw + b"\0", b"XXXXXXXX" + raw[8:], raw[:100] + bytes([raw[100] ^ 1]) + raw[101:]):
+        bad.write_bytes(blob)
+        with pytest.raises(RuntimeError):
+            aw.aw_surrogate_load(ctx, str(bad))
+    with pytest.raises(RuntimeError):
+        aw.aw_surrogate_load(ctx, str(tmp_path / "missing.bin"))
