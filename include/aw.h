@@ -447,9 +447,21 @@ enum { AW_ENGINE_MMA_SYNC = 0, AW_ENGINE_TCGEN05 = 1 };
 int aw_surrogate_set_engine(aw_surrogate *sur, int32_t engine);
 
 /*
+ * aw_surrogate_set_freq_mode - the frequency the inline evaluation of
+ * aw_grid_learned feeds the network.  AW_FREQ_BIN (default): the centre of
+ * the visibility's beam-frequency bin, as the exact tables average the beam
+ * over the bin's channels (Sec. 3.2).  AW_FREQ_CHANNEL: the visibility's own
+ * channel frequency, which removes the channel averaging without any table
+ * memory (the network must have been trained over the band).  Rejected
+ * planes use the exact tables in either mode.  AW_EINVAL for other values.
+ */
+enum { AW_FREQ_BIN = 0, AW_FREQ_CHANNEL = 1 };
+int aw_surrogate_set_freq_mode(aw_surrogate *sur, int32_t mode);
+
+/*
  * aw_surrogate_save - write the surrogate to the file `path` (created or
  * truncated): its configuration, FP32 parameters, the per-w-plane rejection
- * of the last aw_surrogate_tables call and the engine.  Every field is
+ * of the last aw_surrogate_tables call, the engine and the frequency mode.  Every field is
  * little-endian with no padding, after the 8-byte magic "AWSURR01", and the
  * file ends with an FNV-1a 64 checksum of the bytes before it; the layout is
  * the same on every host.  Adam moments are not saved.  Synchronises the

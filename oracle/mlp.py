@@ -110,14 +110,15 @@ def features(du, dv, w, f, chi, D, norm_supports, w_max, f_c, f_h, chi_c, chi_h)
 
 
 def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co, vis, weight=None,
-                fp16_layers=True):
+                fp16_layers=True, per_channel=False):
     """Gridding with the surrogate evaluated at every (visibility, tap) point.
 
     For each gridded visibility (footprint x0, y0 and flip from the oracle's
     coordinate step) the tap (jy, jx) lies at d = (x0 + jx) - X cells from the
     visibility's exact position X = u N dl + N/2 (no oversampling grid); the
     features use its exact |w| and the centres of its beam-frequency and
-    parallactic-angle bins; the network's 2P outputs times out_scale are the
+    parallactic-angle bins (with per_channel: the visibility's own channel
+    frequency instead of its bin centre); the network's 2P outputs times out_scale are the
     Mueller kernel values K_{s,c}, and G[s][y][x] += sum_c K_{s,c} w'_c V'_c.
     With fp16_layers the weights of the tensor-core layers (all but the first)
     are rounded to FP16, as the GPU stores them.
@@ -160,7 +161,8 @@ def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vi
         dv = (co.y0[k] + jy.ravel()) - Y
         nf = du.size
         fb = b % spec.nfb
-        Xf = features(du, dv, np.full(nf, ww), np.full(nf, spec.fbin_freqs[fb]), np.full(nf, spec.pa[a]),
+        fq = freq[chan_of_vis[k]] if per_channel else spec.fbin_freqs[fb]
+        Xf = features(du, dv, np.full(nf, ww), np.full(nf, fq), np.full(nf, spec.pa[a]),
                       D, norm_supports, w_max, f_c, f_h, chi_c, chi_h)
         out, _ = forward(p, sizes, Xf, omega0)
         K = (out[:, 0::2] + 1j * out[:, 1::2]) * out_scale          # [taps][P]

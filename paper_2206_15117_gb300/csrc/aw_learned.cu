@@ -51,6 +51,7 @@ struct LearnArgs {
     const int32_t *bin_support;
     int npa, nfb;
     const double *pa_centres;
+    int freq_channel;         // 1: the visibility's channel frequency, 0: its bin centre
     // surrogate
     const __half *Wh;
     const float *Wf;
@@ -155,10 +156,10 @@ __device__ void stage_chunk(const LearnArgs &a, int4 it, int c0, int cnt, int L,
             e.inv_off = (float)(1.0 / (a.D * (a.norm[pn] / 2 + 1)));
         }
         e.pad1 = 0;
-        // the beam frequency of the visibility's bin: the network was
-        // trained at the bin centres (the exact path averages the beam
-        // over the same channel range)
-        e.f = (float)a.pa_centres[a.npa + bin % a.nfb];
+        // the beam frequency: by default the centre of the visibility's bin
+        // (the exact path averages the beam over the same channel range),
+        // or the visibility's own channel frequency
+        e.f = a.freq_channel ? (float)fq : (float)a.pa_centres[a.npa + bin % a.nfb];
         e.pos = (int)r.x0 | ((int)r.y0 << 16);
         e.koff = ((int)r.fy * a.OS + (int)r.fx) * L * P;
         float2 vv[4] = {};
@@ -760,6 +761,7 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
     a.npa = fallback->spec.npa;
     a.nfb = fallback->spec.nfb;
     a.pa_centres = d_pa;
+    a.freq_channel = s->freq_mode == AW_FREQ_CHANNEL;
     a.Wh = s->d_ph;
     a.Wf = s->d_p;
     for (int l = 0; l < 5; ++l) {

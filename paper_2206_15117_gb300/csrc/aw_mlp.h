@@ -30,6 +30,8 @@ struct aw_surrogate {
     // tensor-core engine of the inline evaluation (AW_ENGINE_*) and its error word
     int engine = AW_ENGINE_TCGEN05;
     unsigned int *d_err = nullptr;
+    // frequency fed to the inline evaluation (AW_FREQ_*)
+    int freq_mode = AW_FREQ_BIN;
 };
 
 int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,

@@ -187,6 +187,13 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *s, const aw_kernel_set *exact
     SUR_GUARD_END
 }
 
+int aw_surrogate_set_freq_mode(aw_surrogate *s, int32_t mode) {
+    if (!s) return aw_set_error(AW_EINVAL, "surrogate is NULL");
+    if (mode != AW_FREQ_BIN && mode != AW_FREQ_CHANNEL) return aw_set_error(AW_EINVAL, "frequency mode %d", mode);
+    s->freq_mode = mode;
+    return AW_OK;
+}
+
 int aw_surrogate_set_engine(aw_surrogate *s, int32_t engine) {
     if (!s) return aw_set_error(AW_EINVAL, "surrogate is NULL");
     if (engine != AW_ENGINE_MMA_SYNC && engine != AW_ENGINE_TCGEN05) return aw_set_error(AW_EINVAL, "engine %d", engine);

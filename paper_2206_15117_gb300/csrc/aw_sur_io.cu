@@ -3,7 +3,7 @@
 //
 // Layout (every field little-endian, no padding):
 //   "AWSURR01"                                  8 bytes
-//   int32 npol, width, n_hidden, norm_nw, engine
+//   int32 npol, width, n_hidden, norm_nw, engine, freq_mode
 //   float32 omega0, out_scale
 //   float64 D, w_max, f_c, f_h, chi_c, chi_h
 //   uint64 seed
@@ -119,6 +119,7 @@ extern "C" int aw_surrogate_save(const aw_surrogate *s, const char *path) {
         w.i32(s->cfg.n_hidden);
         w.i32((int32_t)s->norm.size());
         w.i32(s->engine);
+        w.i32(s->freq_mode);
         w.f32(s->cfg.omega0);
         w.f32(s->cfg.out_scale);
         w.f64(s->cfg.D);
@@ -176,6 +177,7 @@ extern "C" int aw_surrogate_load(aw_ctx *ctx, const char *path, aw_surrogate **o
         cfg.n_hidden = r.i32();
         cfg.norm_nw = r.i32();
         const int32_t engine = r.i32();
+        const int32_t freq_mode = r.i32();
         cfg.omega0 = r.f32();
         cfg.out_scale = r.f32();
         cfg.D = r.f64();
@@ -203,6 +205,8 @@ extern "C" int aw_surrogate_load(aw_ctx *ctx, const char *path, aw_surrogate **o
         if (r.pos != buf.size() - 8) return aw_set_error(AW_EINVAL, "'%s': trailing bytes", path);
         if (engine != AW_ENGINE_MMA_SYNC && engine != AW_ENGINE_TCGEN05)
             return aw_set_error(AW_EINVAL, "'%s': engine %d", path, engine);
+        if (freq_mode != AW_FREQ_BIN && freq_mode != AW_FREQ_CHANNEL)
+            return aw_set_error(AW_EINVAL, "'%s': frequency mode %d", path, freq_mode);
         aw_surrogate *s = nullptr;
         int rc = aw_surrogate_create(ctx, &cfg, &s);
         if (rc) return rc;
@@ -220,6 +224,7 @@ extern "C" int aw_surrogate_load(aw_ctx *ctx, const char *path, aw_surrogate **o
         }
         s->plane_rejected = rej;
         s->engine = engine;
+        s->freq_mode = freq_mode;
         *out = s;
         return AW_OK;
     } catch (const std::bad_alloc &) {

@@ -92,3 +92,33 @@ def test_tensor_core_engines_agree(ctx):
     assert l2 < 2e-3, (l2, mx)
     with pytest.raises(RuntimeError):
         aw.aw_surrogate_set_engine(sur, 7)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_per_channel_frequency_matches_oracle(ctx, engine):
+    # the network fed each visibility's own channel frequency instead of its
+    # beam-frequency bin centre (the case has two channels per bin)
+    from paper_2206_15117_gb300 import aw
+    ob, kw, exact, sur, plan, vis, w, scales, keep = _setup(ctx)
+    aw.aw_surrogate_set_engine(sur, engine)
+    p = aw.aw_surrogate_get_params(sur)
+    sizes = omlp.layer_sizes(5, 128, 4, 16)
+    sc = (scales["D"], scales["norm_supports"], scales["w_max"], scales["f_c"], scales["f_h"], scales["chi_c"],
+          scales["chi_h"], scales["out_scale"])
+    spec = oracle_spec(kw)
+    co = oracle_coords(ob, kw)
+    out = {}
+    for mode in (aw.AW_FREQ_BIN, aw.AW_FREQ_CHANNEL):
+        aw.aw_surrogate_set_freq_mode(sur, mode)
+        grid = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
+        aw.aw_grid_learned(ctx, plan, sur, exact, torch.as_tensor(vis, device="cuda"), torch.as_tensor(w, device="cuda"),
+                           grid)
+        out[mode] = grid.cpu().numpy()
+    G = omlp.grid_inline(p, sizes, 30.0, sc, spec, ob.uvw, ob.row_of_vis, ob.chan_of_vis, ob.freq, co, vis, w,
+                         per_channel=True)
+    l2, mx = rel_err(out[aw.AW_FREQ_CHANNEL], G)
+    assert l2 < 1e-2, (l2, mx)
+    # the mode matters on this case
+    assert rel_err(out[aw.AW_FREQ_BIN], G)[0] > 3 * l2
+    with pytest.raises(RuntimeError):
+        aw.aw_surrogate_set_freq_mode(sur, 2)
