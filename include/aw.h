@@ -436,6 +436,24 @@ int aw_grid_learned(aw_ctx *ctx, const aw_plan *plan, aw_surrogate *sur, const a
                     const void *vis, const float *weight, void *grid, aw_stats *stats, void *stream);
 
 /*
+ * aw_degrid_learned - degridding with the surrogate evaluated inline: for
+ * every valid visibility of the plan and every tap of its footprint the
+ * network (trained on a DEGRID-role set) gives the Mueller kernel K_{c,s} at
+ * the tap's exact offset, exact |w|, frequency (aw_surrogate_set_freq_mode)
+ * and PA bin centre, as in aw_grid_learned; vis_out[c] = sum over taps and s
+ * of K_{c,s} model_s[cell], then P conj() for flipped visibilities, as in
+ * aw_degrid.  Invalid visibilities get 0.  W planes rejected by the last
+ * aw_surrogate_tables call use `fallback` (the exact set, role DEGRID or
+ * ADJOINT, AW_EINVAL otherwise) at the plan's quantised offsets.  model:
+ * device complex64 [npol][N][N]; vis_out: device complex64 [nvis][npol],
+ * overwritten.  Runs on the TCGEN05 engine only (AW_EUNSUPPORTED with
+ * MMA_SYNC); synchronises `stream`; AW_ETIMEOUT if a bounded tensor-core
+ * completion wait gave up (vis_out invalid).
+ */
+int aw_degrid_learned(aw_ctx *ctx, const aw_plan *plan, aw_surrogate *sur, const aw_kernel_set *fallback,
+                      const void *model, void *vis_out, void *stream);
+
+/*
  * aw_surrogate_set_engine - tensor-core generation of the inline evaluation in
  * aw_grid_learned.  AW_ENGINE_TCGEN05 (default): 128-row tiles per CTA,
  * tcgen05.mma with FP32 accumulators in tensor memory, one thread issuing.

@@ -109,51 +109,40 @@ def features(du, dv, w, f, chi, D, norm_supports, w_max, f_c, f_h, chi_c, chi_h)
                      (np.asarray(f) - f_c) / f_h, (np.asarray(chi) - chi_c) / chi_h], axis=-1)
 
 
-def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co, vis, weight=None,
-                fp16_layers=True, per_channel=False):
-    """Gridding with the surrogate evaluated at every (visibility, tap) point.
-
-    For each gridded visibility (footprint x0, y0 and flip from the oracle's
-    coordinate step) the tap (jy, jx) lies at d = (x0 + jx) - X cells from the
-    visibility's exact position X = u N dl + N/2 (no oversampling grid); the
-    features use its exact |w| and the centres of its beam-frequency and
-    parallactic-angle bins (with per_channel: the visibility's own channel
-    frequency instead of its bin centre); the network's 2P outputs times out_scale are the
-    Mueller kernel values K_{s,c}, and G[s][y][x] += sum_c K_{s,c} w'_c V'_c.
-    With fp16_layers the weights of the tensor-core layers (all but the first)
-    are rounded to FP16, as the GPU stores them.
-    `scales` = (D, norm_supports, w_max, f_c, f_h, chi_c, chi_h, out_scale).
-    """
-    from . import core as oc
-    D, norm_supports, w_max, f_c, f_h, chi_c, chi_h, out_scale = scales
+def _fp16_rounded(params, sizes, fp16_layers):
+    """FP64 parameters with the weights of the tensor-core layers (all but the
+    first) rounded to FP16 when fp16_layers, as the GPU stores them."""
     p = np.array(params, np.float64)
     if fp16_layers:
-        layers = unpack(p, sizes)
         pos = sizes[0] * sizes[1] + sizes[1]
         for li in range(1, len(sizes) - 1):
             n_in, n_out = sizes[li], sizes[li + 1]
             p[pos:pos + n_out * n_in] = p[pos:pos + n_out * n_in].astype(np.float16).astype(np.float64)
             pos += n_out * n_in + n_out
-    npol = spec.npol
-    N = spec.N
-    G = np.zeros((npol, N, N), np.complex128)
-    v = np.asarray(vis, np.complex128).reshape(-1, npol)
-    w = np.ones(v.shape, np.float64) if weight is None else np.asarray(weight, np.float64).reshape(-1, npol)
+    return p
+
+
+def _inline_kernels(p, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co, per_channel):
+    """For every valid visibility k (in index order): (k, K) with K the network's
+    kernel [S][S][npol][npol] at the taps of its footprint.  Tap (jy, jx) lies at
+    d = (x0 + jx) - X cells from the visibility's exact position X = u N dl + N/2
+    (u after the w >= 0 flip; no oversampling grid); the features use its exact
+    |w|, the centre of its parallactic-angle bin and the centre of its
+    beam-frequency bin (per_channel: its own channel frequency); the network's
+    2P outputs times out_scale are the P Mueller values."""
+    from . import core as oc
+    D, norm_supports, w_max, f_c, f_h, chi_c, chi_h, out_scale = scales
+    npol, N = spec.npol, spec.N
     f = np.asarray(freq, np.float64)[chan_of_vis] / oc.C_LIGHT
     uvwl = np.asarray(uvw, np.float64)[row_of_vis] * f[:, None]
     for k in np.flatnonzero(co.valid == 1):
-        vk, wk = v[k].copy(), w[k].copy()
         u, vv, ww = uvwl[k]
         if co.flip[k]:
             u, vv, ww = -u, -vv, -ww
-            vk = np.conj(vk)
-            if npol == 4:
-                vk = vk[[0, 2, 1, 3]]
-                wk = wk[[0, 2, 1, 3]]
         X = u * (N * spec.dl) + N // 2
         Y = vv * (N * spec.dl) + N // 2
         b = co.bin[k]
-        pidx = b // (spec.npa * spec.nfb)
+        pidx = spec.plane_of(b)
         a = (b // spec.nfb) % spec.npa
         S = spec.supports[pidx]
         jy, jx = np.meshgrid(np.arange(S), np.arange(S), indexing="ij")
@@ -166,7 +155,54 @@ def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vi
                       D, norm_supports, w_max, f_c, f_h, chi_c, chi_h)
         out, _ = forward(p, sizes, Xf, omega0)
         K = (out[:, 0::2] + 1j * out[:, 1::2]) * out_scale          # [taps][P]
-        K = K.reshape(S, S, npol, npol)                              # [jy][jx][s][c]
-        contrib = np.einsum("yxsc,c->syx", K, wk * vk)
+        yield k, K.reshape(S, S, npol, npol)
+
+
+def grid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co, vis, weight=None,
+                fp16_layers=True, per_channel=False):
+    """Gridding with the surrogate evaluated at every (visibility, tap) point
+    (see _inline_kernels): G[s][y0 + jy][x0 + jx] += sum_c K_{s,c} w'_c V'_c,
+    with V', w' the flipped visibility and weights (V' = P conj V for w < 0).
+    `scales` = (D, norm_supports, w_max, f_c, f_h, chi_c, chi_h, out_scale).
+    """
+    npol, N = spec.npol, spec.N
+    p = _fp16_rounded(params, sizes, fp16_layers)
+    G = np.zeros((npol, N, N), np.complex128)
+    v = np.asarray(vis, np.complex128).reshape(-1, npol)
+    w = np.ones(v.shape, np.float64) if weight is None else np.asarray(weight, np.float64).reshape(-1, npol)
+    for k, K in _inline_kernels(p, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co,
+                                per_channel):
+        vk, wk = v[k].copy(), w[k].copy()
+        if co.flip[k]:
+            vk = np.conj(vk)
+            if npol == 4:
+                vk = vk[[0, 2, 1, 3]]
+                wk = wk[[0, 2, 1, 3]]
+        S = K.shape[0]
+        contrib = np.einsum("yxsc,c->syx", K, wk * vk)              # K [jy][jx][s][c]
         G[:, co.y0[k]:co.y0[k] + S, co.x0[k]:co.x0[k] + S] += contrib
     return G
+
+
+def degrid_inline(params, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co, G,
+                  fp16_layers=True, per_channel=False):
+    """Degridding with the surrogate (trained on degridding kernels) evaluated
+    at every (visibility, tap) point (see _inline_kernels):
+    V_c = sum_taps sum_s K_{c,s} G_s[y0 + jy][x0 + jx], then P conj(V) for a
+    visibility flipped to w >= 0; invalid visibilities give 0.  Returns
+    complex128 [nvis][npol]."""
+    npol = spec.npol
+    p = _fp16_rounded(params, sizes, fp16_layers)
+    G = np.asarray(G, np.complex128)
+    out = np.zeros((co.x0.shape[0], npol), np.complex128)
+    for k, K in _inline_kernels(p, sizes, omega0, scales, spec, uvw, row_of_vis, chan_of_vis, freq, co,
+                                per_channel):
+        S = K.shape[0]
+        win = G[:, co.y0[k]:co.y0[k] + S, co.x0[k]:co.x0[k] + S]   # [s][jy][jx]
+        vk = np.einsum("yxcs,syx->c", K, win)                       # K [jy][jx][c][s]
+        if co.flip[k]:
+            vk = np.conj(vk)
+            if npol == 4:
+                vk = vk[[0, 2, 1, 3]]
+        out[k] = vk
+    return out

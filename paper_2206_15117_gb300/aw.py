@@ -112,6 +112,7 @@ SIGNATURES = {
     "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_set_engine": (ctypes.c_int, [c_p, c_i32]),
     "aw_surrogate_set_freq_mode": (ctypes.c_int, [c_p, c_i32]),
+    "aw_degrid_learned": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_save": (ctypes.c_int, [c_p, ctypes.c_char_p]),
     "aw_surrogate_load": (ctypes.c_int, [c_p, ctypes.c_char_p, ctypes.POINTER(c_p)]),
     "aw_reproject": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(aw_sky_frame), c_p, ctypes.POINTER(aw_sky_frame),
@@ -558,6 +559,11 @@ def aw_surrogate_tables(ctx: Handle, sur: Handle, exact: Handle, reject_rel: flo
 
 def aw_surrogate_set_engine(sur: Handle, engine: int):
     _check(load().aw_surrogate_set_engine(sur.ptr, int(engine)), "aw_surrogate_set_engine")
+
+
+def aw_degrid_learned(ctx: Handle, plan: Handle, sur: Handle, fallback: Handle, model, vis_out, stream=None):
+    _check(load().aw_degrid_learned(ctx.ptr, plan.ptr, sur.ptr, fallback.ptr, _ptr(model), _ptr(vis_out),
+                                    _stream(stream)), "aw_degrid_learned")
 
 
 def aw_surrogate_set_freq_mode(sur: Handle, mode: int):

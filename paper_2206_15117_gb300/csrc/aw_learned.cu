@@ -66,6 +66,10 @@ struct LearnArgs {
     const int64_t *bin_offset;
     int storage, ce;
     float inv_kscale;
+    // degridding: the model grid read and the visibilities written
+    const float2 *model;
+    float2 *vis_out;
+    int64_t nvis, nvalid;
     // statistics / queue
     double *wsum;
     unsigned long long *nonfinite;
@@ -131,7 +135,7 @@ __device__ __forceinline__ void warp_layer(const __half *sAin, const __half *sWl
 // exact coordinates (FP64), flipped and weighted values; the weight sum and
 // the non-finite count are reduced over the block and added to the plan's
 // statistics.  All threads of the block call it.
-template <int NPOL>
+template <int NPOL, bool DEG = false>
 __device__ void stage_chunk(const LearnArgs &a, int4 it, int c0, int cnt, int L, int bin, VisL *sv, double *s_red) {
     constexpr int P = NPOL * NPOL;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -162,6 +166,12 @@ __device__ void stage_chunk(const LearnArgs &a, int4 it, int c0, int cnt, int L,
         e.f = a.freq_channel ? (float)fq : (float)a.pa_centres[a.npa + bin % a.nfb];
         e.pos = (int)r.x0 | ((int)r.y0 << 16);
         e.koff = ((int)r.fy * a.OS + (int)r.fx) * L * P;
+        if constexpr (DEG) {
+            // degridding stages coordinates only
+            for (int c = 0; c < 4; ++c) e.v[c] = make_float2(0.f, 0.f);
+            sv[i] = e;
+            continue;
+        }
         float2 vv[4] = {};
         float ww[4] = {0, 0, 0, 0};
         bool bad = false;
@@ -189,6 +199,7 @@ __device__ void stage_chunk(const LearnArgs &a, int4 it, int c0, int cnt, int L,
         wloc += wm / NPOL;
         sv[i] = e;
     }
+    if constexpr (DEG) return;   // no statistics (every thread returns here)
     for (int o = 16; o; o >>= 1) {
         wloc += __shfl_xor_sync(0xffffffffu, wloc, o);
         nbad += __shfl_xor_sync(0xffffffffu, nbad, o);
@@ -512,7 +523,14 @@ __device__ __forceinline__ void wg_sync(int wg) {
 // reuses the first 32 once the last hidden epilogue has read them) and
 // mbarrier, and an elected thread of each issues its own MMAs: while some
 // warpgroups run epilogues the tensor cores work on another's layer.
-template <int NPOL>
+//
+// DEG: degridding with the same network evaluation.  A point (visibility,
+// tap) gathers the npol model values at its cell and forms sum_s K_{c,s} G_s;
+// the lanes of a warp that hold the same visibility (contiguous) are summed by
+// a segmented shuffle scan and the segment heads add into the chunk's
+// shared-memory accumulators; the chunk's visibilities are then written out
+// (un-flipped), and the visibilities outside the plan's valid range get 0.
+template <int NPOL, bool DEG>
 __global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_kernel(LearnArgs a, unsigned int *err) {
     using Dm = TcDims<NPOL>;
     constexpr int NWG = Dm::NWG;
@@ -528,6 +546,7 @@ __global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_ke
     __shared__ uint32_t s_tmem;
     __shared__ int s_item, s_abort, s_wgab[NWG];
     __shared__ double s_red[4 * NWG];
+    __shared__ float2 s_acc[DEG ? LCHUNK * NPOL : 1];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int wg = warp >> 2, wtid = tid & 127;          // warpgroup, thread within it (= tile row)
     unsigned char *sA = smem + Dm::A_OFF + (size_t)wg * tc::TILE_BYTES;
@@ -594,7 +613,9 @@ __global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_ke
         for (int c0 = 0; c0 < it.y && !s_abort; c0 += LCHUNK) {
             const int cnt = min(LCHUNK, it.y - c0);
             __syncthreads();
-            stage_chunk<NPOL>(a, it, c0, cnt, L, bin, sv, s_red);
+            stage_chunk<NPOL, DEG>(a, it, c0, cnt, L, bin, sv, s_red);
+            if constexpr (DEG)
+                for (int i = tid; i < cnt * NPOL; i += blockDim.x) s_acc[i] = make_float2(0.f, 0.f);
             __syncthreads();
             const int npts = cnt * L;
             // this warpgroup's tiles: NWG k + wg
@@ -691,6 +712,51 @@ __global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_ke
                     }
                 }
                 if (s_wgab[wg]) break;
+                if constexpr (DEG) {
+                    // sum_s K_{c,s} G_s at this point's cell
+                    float2 o[NPOL];
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c) o[c] = make_float2(0.f, 0.f);
+                    if (okp) {
+                        const int pos = sv[vi].pos;
+                        const int gx = (pos & 0xffff) + jx, gy = (pos >> 16) + jy;
+                        float2 gv[NPOL];
+#pragma unroll
+                        for (int s2 = 0; s2 < NPOL; ++s2) gv[s2] = __ldg(a.model + ((int64_t)s2 * a.N + gy) * a.N + gx);
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c)
+#pragma unroll
+                            for (int s2 = 0; s2 < NPOL; ++s2) {
+                                const float kr = kv[2 * (c * NPOL + s2)], ki = kv[2 * (c * NPOL + s2) + 1];
+                                o[c].x += kr * gv[s2].x - ki * gv[s2].y;
+                                o[c].y += kr * gv[s2].y + ki * gv[s2].x;
+                            }
+                    }
+                    // segmented suffix scan over the warp: lanes holding one visibility are
+                    // contiguous; lanes past the chunk get keys of their own
+                    const int lane = tid & 31;
+                    const int key = okp ? vi : (1 << 24) + lane;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int ko = __shfl_down_sync(0xffffffffu, key, off);
+                        const bool same = lane + off < 32 && ko == key;
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c) {
+                            const float tx = __shfl_down_sync(0xffffffffu, o[c].x, off);
+                            const float ty = __shfl_down_sync(0xffffffffu, o[c].y, off);
+                            if (same) { o[c].x += tx; o[c].y += ty; }
+                        }
+                    }
+                    const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+                    if (okp && (lane == 0 || kp != key)) {
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c) {
+                            atomicAdd(&s_acc[vi * NPOL + c].x, o[c].x);
+                            atomicAdd(&s_acc[vi * NPOL + c].y, o[c].y);
+                        }
+                    }
+                    continue;
+                }
                 // apply to the visibility and add to the grid, one row per thread
                 if (okp) {
                     const int pos = sv[vi].pos;
@@ -713,7 +779,32 @@ __global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_ke
             if (tid == 0)
                 for (int g = 0; g < NWG; ++g)
                     if (s_wgab[g]) s_abort = 1;
+            if constexpr (DEG) {
+                // the chunk's visibilities, un-flipped: V -> P conj(V)
+                for (int i = tid; i < cnt; i += blockDim.x) {
+                    const aw_rec r = a.rec[it.x + c0 + i];
+                    float2 out[NPOL];
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c) out[c] = s_acc[i * NPOL + c];
+                    if (r.flip) {
+#pragma unroll
+                        for (int c = 0; c < NPOL; ++c) out[c].y = -out[c].y;
+                        if (NPOL == 4) { const float2 t = out[1]; out[1] = out[2]; out[2] = t; }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c) a.vis_out[(int64_t)r.orig * NPOL + c] = out[c];
+                }
+            }
             __syncthreads();   // s_abort is read by every thread in the loop conditions
+        }
+    }
+    if constexpr (DEG) {
+        // visibilities that were not gridded (outside or flagged) predict zero
+        for (int64_t i = a.nvalid + (int64_t)blockIdx.x * blockDim.x + tid; i < a.nvis;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t o = (int64_t)a.rec[i].orig * NPOL;
+#pragma unroll
+            for (int c = 0; c < NPOL; ++c) a.vis_out[o + c] = make_float2(0.f, 0.f);
         }
     }
     // ---- free the tensor memory (every commit was waited for)
@@ -736,12 +827,15 @@ size_t aw_learned_smem_bytes(int npol) {
 }
 
 int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,
-                           const double *d_pa, const void *vis, const float *weight, void *grid, int sm_count,
-                           cudaStream_t st) {
+                           const double *d_pa, const void *vis, const float *weight, void *grid, const void *model,
+                           void *vis_out, int sm_count, cudaStream_t st) {
+    const bool deg = model != nullptr;
     if (s->cfg.width != LW || s->cfg.n_hidden != 4)
         return aw_set_error(AW_EUNSUPPORTED, "inline evaluation needs width 128 and 4 sine layers");
     if (s->cfg.npol != p->npol) return aw_set_error(AW_EINVAL, "surrogate npol %d, plan npol %d", s->cfg.npol, p->npol);
-    if (p->nitems == 0) return AW_OK;
+    if (deg && s->engine != AW_ENGINE_TCGEN05)
+        return aw_set_error(AW_EUNSUPPORTED, "inline degridding runs on the TCGEN05 engine only");
+    if (deg ? p->nvis == 0 : p->nitems == 0) return AW_OK;
     LearnArgs a;
     a.rec = p->d_rec;
     a.items = p->d_items;
@@ -749,6 +843,10 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
     a.vis = reinterpret_cast<const float2 *>(vis);
     a.weight = weight;
     a.grid = reinterpret_cast<float2 *>(grid);
+    a.model = reinterpret_cast<const float2 *>(model);
+    a.vis_out = reinterpret_cast<float2 *>(vis_out);
+    a.nvis = p->nvis;
+    a.nvalid = p->nvalid;
     a.N = p->N;
     a.OS = p->OS;
     a.uvw = p->vis.uvw;
@@ -788,29 +886,34 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
     a.wsum = p->d_wsum;
     a.nonfinite = p->d_nonfinite;
     a.counter = p->d_counter;
-    AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), st));
-    AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), st));
+    if (!deg) {
+        AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), st));
+        AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), st));
+    }
     AW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st));
-    const int ctas = (int)std::min<int64_t>(p->nitems, sm_count);
+    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(p->nitems, sm_count));
     if (s->engine == AW_ENGINE_TCGEN05) {
         if (!s->d_err) AW_CUDA_TRY(cudaMalloc(&s->d_err, sizeof(unsigned int)));
         AW_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned int), st));
-        if (p->npol == 4) {
-            const size_t sm4 = TcDims<4>::BYTES;
-            AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sm4));
-            grid_learned_tc_kernel<4><<<ctas, 128 * TcDims<4>::NWG, sm4, st>>>(a, s->d_err);
-        } else {
-            const size_t sm1 = TcDims<1>::BYTES;
-            AW_CUDA_TRY(cudaFuncSetAttribute(grid_learned_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sm1));
-            grid_learned_tc_kernel<1><<<ctas, 128 * TcDims<1>::NWG, sm1, st>>>(a, s->d_err);
-        }
+        auto launch = [&](auto kern, size_t bytes, int threads) -> int {
+            AW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+            kern<<<ctas, threads, bytes, st>>>(a, s->d_err);
+            return AW_OK;
+        };
+        int lrc;
+        if (p->npol == 4)
+            lrc = deg ? launch(grid_learned_tc_kernel<4, true>, TcDims<4>::BYTES, 128 * TcDims<4>::NWG)
+                      : launch(grid_learned_tc_kernel<4, false>, TcDims<4>::BYTES, 128 * TcDims<4>::NWG);
+        else
+            lrc = deg ? launch(grid_learned_tc_kernel<1, true>, TcDims<1>::BYTES, 128 * TcDims<1>::NWG)
+                      : launch(grid_learned_tc_kernel<1, false>, TcDims<1>::BYTES, 128 * TcDims<1>::NWG);
+        if (lrc) return lrc;
         AW_CHECK_LAUNCH();
         unsigned int e = 0;
         AW_CUDA_TRY(cudaMemcpyAsync(&e, s->d_err, sizeof(e), cudaMemcpyDeviceToHost, st));
         AW_CUDA_TRY(cudaStreamSynchronize(st));
-        if (e) return aw_set_error(AW_ETIMEOUT, "grid_learned: a tensor-core completion wait gave up; grid invalid");
+        if (e) return aw_set_error(AW_ETIMEOUT, "%s: a tensor-core completion wait gave up; output invalid",
+                                   deg ? "degrid_learned" : "grid_learned");
         return AW_OK;
     }
     const size_t smem = aw_learned_smem_bytes(p->npol);

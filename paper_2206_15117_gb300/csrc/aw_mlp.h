@@ -34,9 +34,11 @@ struct aw_surrogate {
     int freq_mode = AW_FREQ_BIN;
 };
 
+// Inline evaluation: gridding (model == NULL) or, with model and vis_out,
+// degridding (TCGEN05 engine only).
 int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, const uint8_t *d_rejected,
-                           const double *d_pa, const void *vis, const float *weight, void *grid, int sm_count,
-                           cudaStream_t st);
+                           const double *d_pa, const void *vis, const float *weight, void *grid, const void *model,
+                           void *vis_out, int sm_count, cudaStream_t st);
 
 int aw_sur_init(aw_surrogate *s);
 void aw_sur_free(aw_surrogate *s);

@@ -203,17 +203,15 @@ int aw_surrogate_set_engine(aw_surrogate *s, int32_t engine) {
 
 }  // extern "C"
 
-extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback,
-                               const void *vis, const float *weight, void *grid, aw_stats *stats, void *stream) {
-    SUR_GUARD_BEGIN
-    if (!ctx || !p || !s || !fallback || !grid || (!vis && p->nvis)) return aw_set_error(AW_EINVAL, "NULL argument");
+// Checks shared by the inline gridding and degridding, and the upload of the
+// per-plane rejection flags and the bin centres the kernels read.
+static int prepare_inline(const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback, cudaStream_t st) {
     if (p->N != fallback->spec.N || p->OS != fallback->spec.OS || p->nbins != fallback->nbins ||
         p->bin_support != fallback->bin_support || p->npol != fallback->spec.npol)
         return aw_set_error(AW_EINVAL, "fallback kernel set geometry does not match the plan");
     if (fallback->nclass > 1) return aw_set_error(AW_EUNSUPPORTED, "the surrogate has no baseline-class input");
     int rc = set_dev(s->device);
     if (rc) return rc;
-    cudaStream_t st = S_(stream);
     const int nw = fallback->spec.nw, npa = fallback->spec.npa;
     if (!s->d_rejected) AW_CUDA_TRY(cudaMalloc(&s->d_rejected, 256));
     if (!s->d_pa) AW_CUDA_TRY(cudaMalloc(&s->d_pa, sizeof(double) * 256));
@@ -225,7 +223,32 @@ extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, c
     AW_CUDA_TRY(cudaMemcpyAsync(s->d_pa, fallback->pa.data(), sizeof(double) * npa, cudaMemcpyHostToDevice, st));
     AW_CUDA_TRY(cudaMemcpyAsync(s->d_pa + npa, fallback->fbin_freqs.data(), sizeof(double) * fallback->spec.nfb,
                                 cudaMemcpyHostToDevice, st));
-    rc = aw_launch_grid_learned(p, s, fallback, s->d_rejected, s->d_pa, vis, weight, grid, ctx->sm_count, st);
+    return AW_OK;
+}
+
+extern "C" int aw_degrid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback,
+                                 const void *model, void *vis_out, void *stream) {
+    SUR_GUARD_BEGIN
+    if (!ctx || !p || !s || !fallback || !model || (!vis_out && p->nvis)) return aw_set_error(AW_EINVAL, "NULL argument");
+    if (fallback->spec.role != AW_ROLE_DEGRID && fallback->spec.role != AW_ROLE_ADJOINT)
+        return aw_set_error(AW_EINVAL, "the fallback set of degridding must have the DEGRID or ADJOINT role");
+    cudaStream_t st = S_(stream);
+    int rc = prepare_inline(p, s, fallback, st);
+    if (rc) return rc;
+    return aw_launch_grid_learned(p, s, fallback, s->d_rejected, s->d_pa, nullptr, nullptr, nullptr, model, vis_out,
+                                  ctx->sm_count, st);
+    SUR_GUARD_END
+}
+
+extern "C" int aw_grid_learned(aw_ctx *ctx, const aw_plan *p, aw_surrogate *s, const aw_kernel_set *fallback,
+                               const void *vis, const float *weight, void *grid, aw_stats *stats, void *stream) {
+    SUR_GUARD_BEGIN
+    if (!ctx || !p || !s || !fallback || !grid || (!vis && p->nvis)) return aw_set_error(AW_EINVAL, "NULL argument");
+    cudaStream_t st = S_(stream);
+    int rc = prepare_inline(p, s, fallback, st);
+    if (rc) return rc;
+    rc = aw_launch_grid_learned(p, s, fallback, s->d_rejected, s->d_pa, vis, weight, grid, nullptr, nullptr,
+                                ctx->sm_count, st);
     if (rc) return rc;
     if (stats) {
         double ws = 0;

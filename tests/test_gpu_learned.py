@@ -122,3 +122,60 @@ def test_per_channel_frequency_matches_oracle(ctx, engine):
     assert rel_err(out[aw.AW_FREQ_BIN], G)[0] > 3 * l2
     with pytest.raises(RuntimeError):
         aw.aw_surrogate_set_freq_mode(sur, 2)
+
+
+def _setup_degrid(ctx, n_t=10):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=n_t)
+    exact = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID)
+    scales = dict(D=1.0, norm_supports=list(kw["supports"]), w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9,
+                  chi_c=0.0, chi_h=1.5, out_scale=0.02)
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, seed=6, **scales)
+    flags = (np.random.default_rng(40).random(ob.nvis) < 0.05).astype(np.uint8)
+    vd, keep = aw.device_observation(ob, flags=flags)
+    plan = aw.aw_plan_create(ctx, vd, exact)
+    model = sy.random_grid(4, kw["N"], seed=41)
+    co = oc.coords(oracle_spec(kw, oc.ROLE_DEGRID), ob.uvw, ob.row_of_vis, ob.chan_of_vis, ob.freq, ob.pa_bin,
+                   ob.fbin, flags)
+    return ob, kw, exact, sur, plan, model, scales, co, (vd, keep)
+
+
+@pytest.mark.parametrize("freq_mode", [0, 1])
+def test_inline_surrogate_degridding_matches_oracle(ctx, freq_mode):
+    from paper_2206_15117_gb300 import aw
+    ob, kw, exact, sur, plan, model, scales, co, keep = _setup_degrid(ctx)
+    aw.aw_surrogate_set_freq_mode(sur, freq_mode)
+    out = torch.full((ob.nvis, 4), complex(3, 3), dtype=torch.complex64, device="cuda")
+    aw.aw_degrid_learned(ctx, plan, sur, exact, torch.as_tensor(model, device="cuda"), out)
+    got = out.cpu().numpy()
+    p = aw.aw_surrogate_get_params(sur)
+    sc = (scales["D"], scales["norm_supports"], scales["w_max"], scales["f_c"], scales["f_h"], scales["chi_c"],
+          scales["chi_h"], scales["out_scale"])
+    ref = omlp.degrid_inline(p, omlp.layer_sizes(5, 128, 4, 16), 30.0, sc, oracle_spec(kw, oc.ROLE_DEGRID), ob.uvw,
+                             ob.row_of_vis, ob.chan_of_vis, ob.freq, co, model, per_channel=bool(freq_mode))
+    l2, mx = rel_err(got, ref)
+    # FP16 activations between the tensor-core layers, as for inline gridding
+    assert l2 < 1e-2, (l2, mx)
+    assert np.abs(ref).max() > 0
+    assert np.all(got[co.valid == 0] == 0) and (co.valid == 0).any()
+
+
+def test_inline_degridding_rejected_planes_use_exact_tables(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw, exact, sur, plan, model, scales, co, keep = _setup_degrid(ctx)
+    tabs, err, nrej = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=0.0)
+    assert nrej == aw.aw_kernel_set_info(exact).nbins
+    out = torch.empty((ob.nvis, 4), dtype=torch.complex64, device="cuda")
+    aw.aw_degrid_learned(ctx, plan, sur, exact, torch.as_tensor(model, device="cuda"), out)
+    ref = oc.degrid(oc.make_kernels(oracle_spec(kw, oc.ROLE_DEGRID), bins=used_bins(co)), co,
+                    model.astype(np.complex128))
+    l2, mx = rel_err(out.cpu().numpy(), ref)
+    assert l2 < TOL_FP32 and mx < TOL_FP32, (l2, mx)
+    # the other engine and a gridding-role fallback are refused
+    aw.aw_surrogate_set_engine(sur, aw.AW_ENGINE_MMA_SYNC)
+    with pytest.raises(RuntimeError):
+        aw.aw_degrid_learned(ctx, plan, sur, exact, torch.as_tensor(model, device="cuda"), out)
+    aw.aw_surrogate_set_engine(sur, aw.AW_ENGINE_TCGEN05)
+    kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
+    with pytest.raises(RuntimeError):
+        aw.aw_degrid_learned(ctx, plan, sur, kg, torch.as_tensor(model, device="cuda"), out)
