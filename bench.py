@@ -55,6 +55,7 @@ def parse():
                          "32 w-plane kernels (same per-bin density and tables, 1/32 of the memory)")
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
+    ap.add_argument("--no-learned-degrid", action="store_true", help="skip the learned degridding comparison")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
     ap.add_argument("--no-mosaic", action="store_true", help="skip the mosaic measurements")
     ap.add_argument("--no-baselines", action="store_true", help="skip the per-baseline kernel measurement")
@@ -682,6 +683,11 @@ def learned_section(ctx, dev, args):
     gam = torch.empty((Nm, Nm), dtype=torch.float32, device=dev)
     ms_gamma = timed(lambda: aw.mosaic_gamma(ctx, B, 0.2, gam), reps=10)
     net_bytes = aw.aw_surrogate_nparams(sur) * 2
+    degrid = None
+    if not args.no_learned_degrid:
+        del g_ex, g_le, g_ref, fine, plan_f
+        torch.cuda.empty_cache()
+        degrid = learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, chi_c, chi_h)
     return {"workload": "mosaic field 0 of 7 (hexagonal, 1 deg), 2048^2 x 4, 1024 bins (32 w x 8 PA x 4 freq), "
                         "supports 8-64, OS 8; %d of %d visibilities" % (obs.nvis, ob.nvis),
             "mvis_s_learned_with_rejection": obs.nvis / (ms_le / 1e3) / 1e6,
@@ -704,7 +710,71 @@ def learned_section(ctx, dev, args):
             "reject_threshold": reject, "rejected_bins": int(nrej), "nbins": int(len(err)),
             "network_bytes_fp16": int(net_bytes), "exact_table_bytes": int(aw.aw_kernel_set_info(exact).bytes),
             "exact_synthesis_s": t_synth, "surrogate_tables_s": t_tables,
-            "mosaic_gamma_ms_7x2048^2": ms_gamma}
+            "mosaic_gamma_ms_7x2048^2": ms_gamma, "degrid": degrid}
+
+
+def learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, chi_c, chi_h):
+    """Degridding with the surrogate inline on the same field: a second network
+    trained on the exact degridding kernels at 128 w planes, then the model
+    grid of a point-source sky predicted inline (per-plane rejection, and
+    every plane learned) and with the exact 32-plane tables; errors of the
+    predicted visibilities against the exact 128-plane prediction."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    exact = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID)
+    fine = aw.aw_make_kernels(ctx, **kw_fine, role=aw.AW_ROLE_DEGRID)
+    S0 = kw["supports"][0]
+    k0 = torch.empty(kw["OS"] ** 2 * S0 * S0 * 16, dtype=torch.complex64, device=dev)
+    aw.aw_kernel_set_export(exact, 0, k0)
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, D=1.0,
+                                 norm_supports=kw["supports"], w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9,
+                                 chi_c=chi_c, chi_h=chi_h, out_scale=float(k0.abs().max()), seed=18)
+    rep = aw.aw_surrogate_train(ctx, sur, fine, steps=args.learned_steps, batch=65536, lr=3e-4, lr_final=6e-6,
+                                seed=6)
+    tabs, err, nrej = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=0.05)
+    del tabs
+    plan = aw.aw_plan_create(ctx, vd, exact, tune=aw.aw_tune(64, 128, 4, 0))
+    plan_f = aw.aw_plan_create(ctx, vd, fine, tune=aw.aw_tune(64, 128, 4, 0))
+    # a point-source model: 40 sources of 0.1-1 Jy in Stokes I with 5 % Q, U
+    N = kw["N"]
+    rng = np.random.default_rng(21)
+    img = np.zeros((4, N, N), np.float32)
+    qx, qy = rng.integers(N // 4, 3 * N // 4, 40), rng.integers(N // 4, 3 * N // 4, 40)
+    flux = rng.uniform(0.1, 1.0, 40)
+    img[0, qy, qx] = flux
+    img[1, qy, qx] = 0.05 * flux
+    img[2, qy, qx] = -0.05 * flux
+    model = torch.empty((4, N, N), dtype=torch.complex64, device=dev)
+    aw.aw_image_to_grid(ctx, exact, torch.as_tensor(img, device=dev), model)
+    out_ref = torch.empty((obs.nvis, 4), dtype=torch.complex64, device=dev)
+    aw.aw_degrid(ctx, plan_f, fine, model, out_ref)
+    out = torch.empty_like(out_ref)
+    ref_norm = torch.linalg.vector_norm(out_ref)
+
+    def rel():
+        return float(torch.linalg.vector_norm(out - out_ref) / ref_norm)
+
+    ms_ex = timed(lambda: aw.aw_degrid(ctx, plan, exact, model, out))
+    e_ex = rel()
+    ms_rej = timed(lambda: aw.aw_degrid_learned(ctx, plan, sur, exact, model, out), reps=1)
+    e_rej = rel()
+    tabs2, _, _ = aw.aw_surrogate_tables(ctx, sur, exact, reject_rel=1e9)
+    del tabs2
+    ms_all = timed(lambda: aw.aw_degrid_learned(ctx, plan, sur, exact, model, out), reps=1)
+    e_all = rel()
+    n = obs.nvis
+    del exact, fine, plan, plan_f, model, out, out_ref
+    torch.cuda.empty_cache()
+    return {"mvis_s_exact_tables": n / (ms_ex / 1e3) / 1e6, "mvis_s_learned_with_rejection": n / (ms_rej / 1e3) / 1e6,
+            "mvis_s_learned_inline_all_planes": n / (ms_all / 1e3) / 1e6,
+            "degrid_ms_exact": ms_ex, "degrid_ms_learned_with_rejection": ms_rej,
+            "degrid_ms_learned_inline_all_planes": ms_all,
+            "reference": "exact degridding kernels at 128 w planes; relative L2 error of the predicted visibilities "
+                         "of a 40-source model",
+            "vis_rel_err_exact_32_planes": e_ex, "vis_rel_err_learned_with_rejection": e_rej,
+            "vis_rel_err_learned_all_planes": e_all, "rejected_bins": int(nrej), "nbins": int(len(err)),
+            "train": {"steps": rep.steps, "seconds": rep.seconds, "loss_first": rep.loss_first,
+                      "loss_last": rep.loss_last, "set": "exact degridding kernels at 128 w planes x 8 PA x 4 freq"}}
 
 
 # ----------------------------------------------------------------------------- GPU arm
