@@ -682,6 +682,29 @@ int aw_clean(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kgrid, const aw_ke
              const void *vis, const float *weight, const aw_clean_cfg *cfg, float *model, float *residual,
              float *psf, aw_clean_report *report, void *stream);
 
+/* ---- failure injection and self-tests ------------------------------------- */
+/*
+ * aw_debug_fail_alloc - failure injection on the host: n >= 0 makes the n-th
+ * device allocation of the library from now (0 = the next) fail as if the
+ * device were out of memory, once; the call that made it returns AW_ENOMEM
+ * and frees what it had allocated.  n = -1 disarms.  Process-wide.
+ *
+ * aw_debug_alloc_stats - device buffers the library holds now (*live) and
+ * device allocations it has attempted since the process started (*calls).
+ *
+ * aw_debug_wait_timeout - run one of the library's bounded device waits
+ * against a condition that never becomes true, on `stream`: which = 0, the
+ * grid barrier of the cooperative Hogbom kernel (one block waits for a second
+ * arrival); which = 1, the mbarrier completion wait of the tensor-core
+ * kernels (an mbarrier that nothing arrives on).  Returns AW_ETIMEOUT when the
+ * wait gave up as designed (the barrier after about 9 s, the mbarrier after
+ * about 1 s on GB300), AW_OK if it did not;
+ * the context stays usable.  Synchronises `stream`.
+ */
+int aw_debug_fail_alloc(int64_t n);
+int aw_debug_alloc_stats(int64_t *live, int64_t *calls);
+int aw_debug_wait_timeout(aw_ctx *ctx, int32_t which, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,9 @@ SIGNATURES = {
     "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_set_engine": (ctypes.c_int, [c_p, c_i32]),
     "aw_surrogate_set_freq_mode": (ctypes.c_int, [c_p, c_i32]),
+    "aw_debug_fail_alloc": (ctypes.c_int, [c_i64]),
+    "aw_debug_alloc_stats": (ctypes.c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    "aw_debug_wait_timeout": (ctypes.c_int, [c_p, c_i32, c_p]),
     "aw_degrid_learned": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_save": (ctypes.c_int, [c_p, ctypes.c_char_p]),
     "aw_surrogate_load": (ctypes.c_int, [c_p, ctypes.c_char_p, ctypes.POINTER(c_p)]),
@@ -586,3 +589,19 @@ def aw_grid_learned(ctx: Handle, plan: Handle, sur: Handle, fallback: Handle, vi
     _check(load().aw_grid_learned(ctx.ptr, plan.ptr, sur.ptr, fallback.ptr, _ptr(vis), _ptr(weight), _ptr(grid),
                                   ctypes.byref(st) if st is not None else None, _stream(stream)), "aw_grid_learned")
     return st
+
+
+def aw_debug_fail_alloc(n: int):
+    _check(load().aw_debug_fail_alloc(int(n)), "aw_debug_fail_alloc")
+
+
+def aw_debug_alloc_stats():
+    """(live device buffers, device allocations attempted)"""
+    live, calls = c_i64(), c_i64()
+    _check(load().aw_debug_alloc_stats(ctypes.byref(live), ctypes.byref(calls)), "aw_debug_alloc_stats")
+    return live.value, calls.value
+
+
+def aw_debug_wait_timeout(ctx: Handle, which: int, stream=None) -> int:
+    """Status code of the bounded-wait self-test (AW_ETIMEOUT is the expected outcome)."""
+    return int(load().aw_debug_wait_timeout(ctx.ptr, int(which), _stream(stream)))

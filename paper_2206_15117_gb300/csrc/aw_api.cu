@@ -1,5 +1,6 @@
 // C ABI entry points of libaw (declared in include/aw.h): argument checks,
 // handle management, and dispatch to the kernels of the other units.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,28 @@ int aw_mosaic_gamma_impl(aw_ctx *ctx, const float *beams, int nfield, int N, flo
 
 static thread_local char g_err[1024] = "";
 
+// ---------------------------------------------------------------- device memory hook
+static std::atomic<long long> g_alloc_calls{0};   // device allocations attempted
+static std::atomic<long long> g_alloc_live{0};    // buffers allocated and not freed
+static std::atomic<long long> g_alloc_fail_at{-1};  // g_alloc_calls value that fails, or -1
+
+cudaError_t aw_dev_malloc_raw(void **p, size_t bytes) {
+    const long long k = g_alloc_calls.fetch_add(1);
+    if (k == g_alloc_fail_at.load()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;   // injected: nothing was allocated
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_alloc_live.fetch_add(1);
+    return e;
+}
+
+void aw_dev_free(void *p) {
+    if (!p) return;
+    cudaFree(p);
+    g_alloc_live.fetch_sub(1);
+}
+
 int aw_set_error(int code, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -31,7 +54,9 @@ int aw_set_error(int code, const char *fmt, ...) {
     return code;
 }
 
-#define AW_GUARD_BEGIN try {
+#define AW_GUARD_BEGIN \
+    AW_TRACE();         \
+    try {
 #define AW_GUARD_END                                                   \
     }                                                                  \
     catch (const std::bad_alloc &) {                                   \
@@ -77,7 +102,7 @@ int aw_create(aw_ctx **ctx, int device) {
     aw_ctx *c = new aw_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-    cudaError_t e = cudaMalloc(&c->d_scratch, 256);
+    cudaError_t e = aw_dev_malloc(&c->d_scratch, 256);
     if (e != cudaSuccess) {
         delete c;
         return aw_set_error(AW_ENOMEM, "context scratch: %s", cudaGetErrorString(e));
@@ -92,8 +117,8 @@ int aw_destroy(aw_ctx *ctx) {
     if (!ctx) return AW_OK;
     use_device(ctx->device);
     for (auto &kv : ctx->fft_plans) cufftDestroy(kv.second);
-    for (auto &kv : ctx->gridcorr) cudaFree(kv.second);
-    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    for (auto &kv : ctx->gridcorr) aw_dev_free(kv.second);
+    if (ctx->d_scratch) aw_dev_free(ctx->d_scratch);
     delete ctx;
     return AW_OK;
     AW_GUARD_END
@@ -101,9 +126,9 @@ int aw_destroy(aw_ctx *ctx) {
 
 static void free_kset(aw_kernel_set *k) {
     if (!k) return;
-    if (k->d_table) cudaFree(k->d_table);
-    if (k->d_bin_support) cudaFree(k->d_bin_support);
-    if (k->d_bin_offset) cudaFree(k->d_bin_offset);
+    if (k->d_table) aw_dev_free(k->d_table);
+    if (k->d_bin_support) aw_dev_free(k->d_bin_support);
+    if (k->d_bin_offset) aw_dev_free(k->d_bin_offset);
     delete k;
 }
 
@@ -198,14 +223,14 @@ int aw_kernel_set_destroy(aw_kernel_set *k) {
 static void free_plan(aw_plan *p) {
     if (!p) return;
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->d_rec) cudaFree(p->d_rec);
-    if (p->d_items) cudaFree(p->d_items);
-    if (p->d_rec_dg) cudaFree(p->d_rec_dg);
-    if (p->d_items_dg) cudaFree(p->d_items_dg);
-    if (p->d_plane_support) cudaFree(p->d_plane_support);
-    if (p->d_wsum) cudaFree(p->d_wsum);
-    if (p->d_nonfinite) cudaFree(p->d_nonfinite);
-    if (p->d_counter) cudaFree(p->d_counter);
+    if (p->d_rec) aw_dev_free(p->d_rec);
+    if (p->d_items) aw_dev_free(p->d_items);
+    if (p->d_rec_dg) aw_dev_free(p->d_rec_dg);
+    if (p->d_items_dg) aw_dev_free(p->d_items_dg);
+    if (p->d_plane_support) aw_dev_free(p->d_plane_support);
+    if (p->d_wsum) aw_dev_free(p->d_wsum);
+    if (p->d_nonfinite) aw_dev_free(p->d_nonfinite);
+    if (p->d_counter) aw_dev_free(p->d_counter);
     delete p;
 }
 
@@ -382,9 +407,9 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
     cudaStream_t s = S_(stream);
     const size_t gbytes = sizeof(float2) * (size_t)k->spec.npol * k->spec.N * k->spec.N;
     void *grid = nullptr, *v = nullptr;
-    AW_CUDA_TRY(cudaMalloc(&grid, gbytes));
-    cudaError_t e = cudaMalloc(&v, sizeof(float2) * (size_t)k->spec.npol * std::max<int64_t>(vis->nvis, 1));
-    if (e != cudaSuccess) { cudaFree(grid); return aw_set_error(AW_ENOMEM, "autotune vis buffer"); }
+    AW_CUDA_TRY(aw_dev_malloc(&grid, gbytes));
+    cudaError_t e = aw_dev_malloc(&v, sizeof(float2) * (size_t)k->spec.npol * std::max<int64_t>(vis->nvis, 1));
+    if (e != cudaSuccess) { aw_dev_free(grid); return aw_set_error(AW_ENOMEM, "autotune vis buffer"); }
     cudaMemsetAsync(v, 0, sizeof(float2) * (size_t)k->spec.npol * std::max<int64_t>(vis->nvis, 1), s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -448,8 +473,8 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(grid);
-    cudaFree(v);
+    aw_dev_free(grid);
+    aw_dev_free(v);
     if (rc) return rc;
     *out = bt;
     ctx->tune_cache = bt;
@@ -480,3 +505,31 @@ int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, flo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- failure injection and self-tests
+int aw_barrier_selftest(aw_ctx *ctx, cudaStream_t s);
+int aw_mbar_selftest(cudaStream_t st);
+
+extern "C" int aw_debug_fail_alloc(int64_t n) {
+    if (n < -1) return aw_set_error(AW_EINVAL, "n = %lld", (long long)n);
+    g_alloc_fail_at.store(n < 0 ? -1 : g_alloc_calls.load() + n);
+    return AW_OK;
+}
+
+extern "C" int aw_debug_alloc_stats(int64_t *live, int64_t *calls) {
+    if (!live || !calls) return aw_set_error(AW_EINVAL, "NULL argument");
+    *live = g_alloc_live.load();
+    *calls = g_alloc_calls.load();
+    return AW_OK;
+}
+
+extern "C" int aw_debug_wait_timeout(aw_ctx *ctx, int32_t which, void *stream) {
+    AW_GUARD_BEGIN
+    if (!ctx) return aw_set_error(AW_EINVAL, "ctx is NULL");
+    int rc = use_device(ctx->device);
+    if (rc) return rc;
+    if (which == 0) return aw_barrier_selftest(ctx, S_(stream));
+    if (which == 1) return aw_mbar_selftest(S_(stream));
+    return aw_set_error(AW_EINVAL, "which = %d", which);
+    AW_GUARD_END
+}

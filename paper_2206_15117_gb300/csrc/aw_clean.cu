@@ -40,7 +40,7 @@ constexpr int SCR_NITER = 7;     // Hogbom iterations
 constexpr int SCR_BAR_COUNT = 8; // grid barrier: arrivals
 constexpr int SCR_BAR_GEN = 9;   // grid barrier: generation
 constexpr int SCR_BAR_ERR = 10;  // grid barrier: set when a wait gave up
-// spin limit of one barrier wait: 2^24 polls of >= 64 ns, about a second or more
+// spin limit of one barrier wait: 2^24 polls with a 64 ns back-off, about 9 s on GB300
 constexpr long long BAR_SPIN_LIMIT = 1ll << 24;
 
 // ---------------------------------------------------------------- sidelobe
@@ -176,6 +176,13 @@ __device__ bool grid_barrier(unsigned int *scr, unsigned int nblocks, int *s_ok)
     return *s_ok != 0;
 }
 
+// Self-test of the barrier's bounded wait: one block that expects a second
+// arrival which never comes (the arrival count is never reached).
+__global__ void barrier_timeout_kernel(unsigned int *scr) {
+    __shared__ int s_ok;
+    grid_barrier(scr, 2u, &s_ok);
+}
+
 // Maximum of tile t over its window pixels, by one block, reading the
 // residual through L2 (other blocks write it between grid barriers).
 __device__ unsigned long long tile_scan_l2(const float *R0, const HbGeom &g, int t, unsigned long long *red) {
@@ -307,6 +314,19 @@ HbGeom geom_of(int N, const int32_t *win) {
     return g;
 }
 
+// Run barrier_timeout_kernel: AW_ETIMEOUT once the wait has given up.
+int barrier_selftest_impl(aw_ctx *ctx, cudaStream_t s) {
+    AW_CUDA_TRY(cudaMemsetAsync(ctx->d_scratch + SCR_BAR_COUNT, 0, 3 * sizeof(unsigned int), s));
+    barrier_timeout_kernel<<<1, 32, 0, s>>>(ctx->d_scratch);
+    AW_CHECK_LAUNCH();
+    unsigned int w = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&w, ctx->d_scratch + SCR_BAR_ERR, sizeof(w), cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    AW_CUDA_TRY(cudaMemsetAsync(ctx->d_scratch + SCR_BAR_COUNT, 0, 3 * sizeof(unsigned int), s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    return w ? aw_set_error(AW_ETIMEOUT, "grid barrier wait gave up") : AW_OK;
+}
+
 int hogbom_impl(aw_ctx *ctx, float *R, const float *psf, int npol, int N, float gain, float thr, int max_iter,
                 int h, const int32_t *win, float *model, int32_t *n_iter, cudaStream_t s) {
     HbGeom g = geom_of(N, win);
@@ -362,7 +382,7 @@ int window_peak_impl(aw_ctx *ctx, const float *img, int N, const int32_t *win, f
 
 struct DevMem {
     void *p = nullptr;
-    ~DevMem() { if (p) cudaFree(p); }
+    ~DevMem() { if (p) aw_dev_free(p); }
 };
 
 int check_plan_kset(const aw_plan *p, const aw_kernel_set *k) {
@@ -373,7 +393,9 @@ int check_plan_kset(const aw_plan *p, const aw_kernel_set *k) {
     return AW_OK;
 }
 
-#define CL_GUARD_BEGIN try {
+#define CL_GUARD_BEGIN \
+    AW_TRACE();         \
+    try {
 #define CL_GUARD_END                                                   \
     }                                                                  \
     catch (const std::bad_alloc &) {                                   \
@@ -384,6 +406,8 @@ int check_plan_kset(const aw_plan *p, const aw_kernel_set *k) {
     }
 
 }  // namespace
+
+int aw_barrier_selftest(aw_ctx *ctx, cudaStream_t s) { return barrier_selftest_impl(ctx, s); }
 
 extern "C" {
 
@@ -470,8 +494,8 @@ int aw_clean(aw_ctx *ctx, aw_plan *p, const aw_kernel_set *kg, const aw_kernel_s
     const int64_t plane = (int64_t)N * N;
     const size_t vbytes = sizeof(float2) * (size_t)npol * (size_t)std::max<int64_t>(p->nvis, 1);
     DevMem rv, gr;
-    AW_CUDA_TRY(cudaMalloc(&rv.p, vbytes));
-    AW_CUDA_TRY(cudaMalloc(&gr.p, sizeof(float2) * (size_t)npol * plane));
+    AW_CUDA_TRY(aw_dev_malloc(&rv.p, vbytes));
+    AW_CUDA_TRY(aw_dev_malloc(&gr.p, sizeof(float2) * (size_t)npol * plane));
     float2 *res_vis = reinterpret_cast<float2 *>(rv.p);
     aw_clean_report rep{};
     aw_stats st{};

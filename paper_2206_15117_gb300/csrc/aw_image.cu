@@ -99,7 +99,7 @@ int aw_ctx_gridcorr(aw_ctx *ctx, int N, double W, float **out) {
     std::vector<float> c(N);
     for (int q = 0; q < N; ++q) c[q] = (q == 0) ? 0.f : (float)p.eval((q - N / 2) * 2.0 / N);
     float *d = nullptr;
-    AW_CUDA_TRY(cudaMalloc(&d, sizeof(float) * N));
+    AW_CUDA_TRY(aw_dev_malloc(&d, sizeof(float) * N));
     AW_CUDA_TRY(cudaMemcpy(d, c.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
     ctx->gridcorr[key] = d;
     *out = d;

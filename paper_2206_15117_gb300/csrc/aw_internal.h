@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdarg>
@@ -39,6 +40,27 @@ int aw_set_error(int code, const char *fmt, ...);
     } while (0)
 
 #define AW_CHECK_LAUNCH() AW_CUDA_TRY(cudaGetLastError())
+
+// ---------------------------------------------------------------- tracing
+// An NVTX range named after the ABI function for the duration of the call
+// (visible to profilers that attach; free otherwise).
+struct AwTrace {
+    explicit AwTrace(const char *name) { nvtxRangePushA(name); }
+    ~AwTrace() { nvtxRangePop(); }
+    AwTrace(const AwTrace &) = delete;
+    AwTrace &operator=(const AwTrace &) = delete;
+};
+#define AW_TRACE() AwTrace aw_trace_(__func__)
+
+// ---------------------------------------------------------------- device memory
+// Every device buffer of the library goes through these: they count the live
+// buffers and let aw_debug_fail_alloc make a chosen allocation fail.
+cudaError_t aw_dev_malloc_raw(void **p, size_t bytes);
+void aw_dev_free(void *p);
+template <class T>
+inline cudaError_t aw_dev_malloc(T **p, size_t bytes) {
+    return aw_dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
 
 // ---------------------------------------------------------------- handles
 struct aw_ctx {

@@ -500,6 +500,19 @@ __device__ __forceinline__ void st8(unsigned char *tile, int r, int k0, const fl
 
 }  // namespace tc
 
+// Self-test of the bounded mbarrier wait: an mbarrier that nothing arrives on.
+__global__ void mbar_timeout_kernel(unsigned int *err) {
+    __shared__ __align__(8) unsigned long long mbar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::su32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(tc::su32(&mbar), 0)) atomicExch(err, 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(tc::su32(&mbar)) : "memory");
+}
+
 template <int NPOL>
 struct TcDims {
     static constexpr int P = NPOL * NPOL;
@@ -819,6 +832,23 @@ __global__ void __launch_bounds__(128 * TcDims<NPOL>::NWG, 1) grid_learned_tc_ke
 
 }  // namespace
 
+// Run mbar_timeout_kernel: AW_ETIMEOUT once the wait has given up.
+int aw_mbar_selftest(cudaStream_t st) {
+    unsigned int *d = nullptr;
+    AW_CUDA_TRY(aw_dev_malloc(&d, sizeof(unsigned int)));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        mbar_timeout_kernel<<<1, 32, 0, st>>>(d);
+        e = cudaGetLastError();
+    }
+    unsigned int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    aw_dev_free(d);
+    if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "mbarrier self-test: %s", cudaGetErrorString(e));
+    return h ? aw_set_error(AW_ETIMEOUT, "mbarrier wait gave up") : AW_OK;
+}
+
 size_t aw_learned_smem_bytes(int npol) {
     const int P = npol * npol;
     const int NOUT = (2 * P + 7) / 8 * 8;
@@ -893,7 +923,7 @@ int aw_launch_grid_learned(const aw_plan *p, aw_surrogate *s, const aw_kernel_se
     AW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), st));
     const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(p->nitems, sm_count));
     if (s->engine == AW_ENGINE_TCGEN05) {
-        if (!s->d_err) AW_CUDA_TRY(cudaMalloc(&s->d_err, sizeof(unsigned int)));
+        if (!s->d_err) AW_CUDA_TRY(aw_dev_malloc(&s->d_err, sizeof(unsigned int)));
         AW_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(unsigned int), st));
         auto launch = [&](auto kern, size_t bytes, int threads) -> int {
             AW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));

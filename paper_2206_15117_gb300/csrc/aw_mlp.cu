@@ -294,7 +294,7 @@ int nblk(int64_t n, int t = 256) {
 // ------------------------------------------------------------------ surrogate
 int aw_sur_alloc_work(aw_surrogate *s, int B) {
     if (B <= s->bcap) return AW_OK;
-    for (float *p : s->work) cudaFree(p);
+    for (float *p : s->work) aw_dev_free(p);
     s->work.clear();
     const int L = (int)s->sizes.size() - 1;
     // X, T, Z[l], H[l+1], dZ (max width), dH (max width)
@@ -302,7 +302,7 @@ int aw_sur_alloc_work(aw_surrogate *s, int B) {
     for (int w : s->sizes) maxw = std::max(maxw, w);
     auto add = [&](int64_t n) -> float * {
         float *p = nullptr;
-        if (cudaMalloc(&p, sizeof(float) * std::max<int64_t>(n, 1)) != cudaSuccess) return nullptr;
+        if (aw_dev_malloc(&p, sizeof(float) * std::max<int64_t>(n, 1)) != cudaSuccess) return nullptr;
         s->work.push_back(p);
         return p;
     };
@@ -416,14 +416,14 @@ static FeatureScales scales_of(const aw_surrogate *s) {
 struct DevBins {
     double *pa = nullptr, *freq = nullptr;
     ~DevBins() {
-        if (pa) cudaFree(pa);
-        if (freq) cudaFree(freq);
+        if (pa) aw_dev_free(pa);
+        if (freq) aw_dev_free(freq);
     }
 };
 
 static int upload_bins(const aw_kernel_set *k, DevBins &d) {
-    AW_CUDA_TRY(cudaMalloc(&d.pa, sizeof(double) * k->pa.size()));
-    AW_CUDA_TRY(cudaMalloc(&d.freq, sizeof(double) * k->fbin_freqs.size()));
+    AW_CUDA_TRY(aw_dev_malloc(&d.pa, sizeof(double) * k->pa.size()));
+    AW_CUDA_TRY(aw_dev_malloc(&d.freq, sizeof(double) * k->fbin_freqs.size()));
     AW_CUDA_TRY(cudaMemcpy(d.pa, k->pa.data(), sizeof(double) * k->pa.size(), cudaMemcpyHostToDevice));
     AW_CUDA_TRY(cudaMemcpy(d.freq, k->fbin_freqs.data(), sizeof(double) * k->fbin_freqs.size(), cudaMemcpyHostToDevice));
     return AW_OK;
@@ -442,7 +442,7 @@ int aw_sur_train(aw_surrogate *s, const aw_kernel_set *k, const aw_train_cfg *tc
     const SetView v = view_of(k, db.pa, db.freq);
     const FeatureScales fs = scales_of(s);
     double *d_loss = nullptr;
-    AW_CUDA_TRY(cudaMalloc(&d_loss, sizeof(double) * std::max(1, tc->steps)));
+    AW_CUDA_TRY(aw_dev_malloc(&d_loss, sizeof(double) * std::max(1, tc->steps)));
     AW_CUDA_TRY(cudaMemsetAsync(d_loss, 0, sizeof(double) * std::max(1, tc->steps), st));
     const auto t0 = std::chrono::steady_clock::now();
     for (int it = 0; it < tc->steps && rc == AW_OK; ++it) {
@@ -465,7 +465,7 @@ int aw_sur_train(aw_surrogate *s, const aw_kernel_set *k, const aw_train_cfg *tc
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = aw_set_error(AW_ECUDA, "train: %s", cudaGetErrorString(e));
     }
-    cudaFree(d_loss);
+    aw_dev_free(d_loss);
     if (rc) return rc;
     const auto t1 = std::chrono::steady_clock::now();
     if (rep) {
@@ -495,7 +495,7 @@ int aw_sur_tables(aw_surrogate *s, const aw_kernel_set *exact, aw_kernel_set *ou
     const SetView v = view_of(exact, db.pa, db.freq);
     const FeatureScales fs = scales_of(s);
     double *d_err = nullptr;
-    AW_CUDA_TRY(cudaMalloc(&d_err, sizeof(double) * 2 * exact->nbins));
+    AW_CUDA_TRY(aw_dev_malloc(&d_err, sizeof(double) * 2 * exact->nbins));
     AW_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(double) * 2 * exact->nbins, st));
     for (int b = 0; b < exact->nbins && rc == AW_OK; ++b) {
         const int S = exact->bin_support[b];
@@ -520,7 +520,7 @@ int aw_sur_tables(aw_surrogate *s, const aw_kernel_set *exact, aw_kernel_set *ou
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = aw_set_error(AW_ECUDA, "tables: %s", cudaGetErrorString(e));
     }
-    cudaFree(d_err);
+    aw_dev_free(d_err);
     if (rc) return rc;
     // per-w-plane rejection: the worst bin of a plane decides for the plane
     const int per = exact->spec.npa * exact->spec.nfb;
@@ -571,7 +571,7 @@ int aw_sur_init(aw_surrogate *s) {
     // the normalisation layout is owned by the surrogate from here on
     s->norm.assign(s->cfg.norm_supports, s->cfg.norm_supports + s->cfg.norm_nw);
     s->cfg.norm_supports = s->norm.data();
-    AW_CUDA_TRY(cudaMalloc(&s->d_norm, sizeof(int32_t) * s->norm.size()));
+    AW_CUDA_TRY(aw_dev_malloc(&s->d_norm, sizeof(int32_t) * s->norm.size()));
     AW_CUDA_TRY(cudaMemcpy(s->d_norm, s->norm.data(), sizeof(int32_t) * s->norm.size(), cudaMemcpyHostToDevice));
     s->sizes.clear();
     s->sizes.push_back(5);
@@ -588,11 +588,11 @@ int aw_sur_init(aw_surrogate *s) {
         pos += s->sizes[l + 1];
     }
     s->nparam = pos;
-    AW_CUDA_TRY(cudaMalloc(&s->d_p, sizeof(float) * pos));
-    AW_CUDA_TRY(cudaMalloc(&s->d_m, sizeof(float) * pos));
-    AW_CUDA_TRY(cudaMalloc(&s->d_v, sizeof(float) * pos));
-    AW_CUDA_TRY(cudaMalloc(&s->d_g, sizeof(float) * pos));
-    AW_CUDA_TRY(cudaMalloc(&s->d_ph, sizeof(__half) * pos));
+    AW_CUDA_TRY(aw_dev_malloc(&s->d_p, sizeof(float) * pos));
+    AW_CUDA_TRY(aw_dev_malloc(&s->d_m, sizeof(float) * pos));
+    AW_CUDA_TRY(aw_dev_malloc(&s->d_v, sizeof(float) * pos));
+    AW_CUDA_TRY(aw_dev_malloc(&s->d_g, sizeof(float) * pos));
+    AW_CUDA_TRY(aw_dev_malloc(&s->d_ph, sizeof(__half) * pos));
     // SIREN initialisation (Sitzmann et al. 2020): first layer U(-1/in, 1/in),
     // later layers U(-sqrt(6/in)/omega0, +); biases likewise; host SplitMix64
     std::vector<float> h(pos);
@@ -619,14 +619,14 @@ int aw_sur_init(aw_surrogate *s) {
 }
 
 void aw_sur_free(aw_surrogate *s) {
-    for (float *p : s->work) cudaFree(p);
-    if (s->d_rejected) cudaFree(s->d_rejected);
-    if (s->d_err) cudaFree(s->d_err);
-    if (s->d_pa) cudaFree(s->d_pa);
-    if (s->d_norm) cudaFree(s->d_norm);
-    if (s->d_p) cudaFree(s->d_p);
-    if (s->d_m) cudaFree(s->d_m);
-    if (s->d_v) cudaFree(s->d_v);
-    if (s->d_g) cudaFree(s->d_g);
-    if (s->d_ph) cudaFree(s->d_ph);
+    for (float *p : s->work) aw_dev_free(p);
+    if (s->d_rejected) aw_dev_free(s->d_rejected);
+    if (s->d_err) aw_dev_free(s->d_err);
+    if (s->d_pa) aw_dev_free(s->d_pa);
+    if (s->d_norm) aw_dev_free(s->d_norm);
+    if (s->d_p) aw_dev_free(s->d_p);
+    if (s->d_m) aw_dev_free(s->d_m);
+    if (s->d_v) aw_dev_free(s->d_v);
+    if (s->d_g) aw_dev_free(s->d_g);
+    if (s->d_ph) aw_dev_free(s->d_ph);
 }

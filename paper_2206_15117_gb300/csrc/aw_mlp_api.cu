@@ -10,7 +10,9 @@ int aw_kernel_set_alloc(aw_kernel_set *ks);
 
 static inline cudaStream_t S_(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-#define SUR_GUARD_BEGIN try {
+#define SUR_GUARD_BEGIN \
+    AW_TRACE();         \
+    try {
 #define SUR_GUARD_END                                                  \
     }                                                                  \
     catch (const std::bad_alloc &) {                                   \
@@ -125,7 +127,7 @@ int aw_surrogate_loss_grad(aw_ctx *ctx, aw_surrogate *s, const float *X, const f
     if (rc) return rc;
     cudaStream_t st = S_(stream);
     double *d_loss = nullptr;
-    AW_CUDA_TRY(cudaMalloc(&d_loss, sizeof(double)));
+    AW_CUDA_TRY(aw_dev_malloc(&d_loss, sizeof(double)));
     cudaMemsetAsync(d_loss, 0, sizeof(double), st);
     rc = aw_sur_forward(s, X, B, st);
     if (rc == AW_OK) rc = aw_sur_backward(s, X, T, B, d_loss, st);
@@ -135,7 +137,7 @@ int aw_surrogate_loss_grad(aw_ctx *ctx, aw_surrogate *s, const float *X, const f
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = aw_set_error(AW_ECUDA, "loss_grad: %s", cudaGetErrorString(e));
     }
-    cudaFree(d_loss);
+    aw_dev_free(d_loss);
     return rc;
     SUR_GUARD_END
 }
@@ -176,9 +178,9 @@ int aw_surrogate_tables(aw_ctx *ctx, aw_surrogate *s, const aw_kernel_set *exact
     }
     if (rc == AW_OK) rc = aw_sur_tables(s, exact, k, reject_rel, bin_err, S_(stream));
     if (rc != AW_OK) {
-        if (k->d_table) cudaFree(k->d_table);
-        if (k->d_bin_support) cudaFree(k->d_bin_support);
-        if (k->d_bin_offset) cudaFree(k->d_bin_offset);
+        if (k->d_table) aw_dev_free(k->d_table);
+        if (k->d_bin_support) aw_dev_free(k->d_bin_support);
+        if (k->d_bin_offset) aw_dev_free(k->d_bin_offset);
         delete k;
         return rc;
     }
@@ -213,8 +215,8 @@ static int prepare_inline(const aw_plan *p, aw_surrogate *s, const aw_kernel_set
     int rc = set_dev(s->device);
     if (rc) return rc;
     const int nw = fallback->spec.nw, npa = fallback->spec.npa;
-    if (!s->d_rejected) AW_CUDA_TRY(cudaMalloc(&s->d_rejected, 256));
-    if (!s->d_pa) AW_CUDA_TRY(cudaMalloc(&s->d_pa, sizeof(double) * 256));
+    if (!s->d_rejected) AW_CUDA_TRY(aw_dev_malloc(&s->d_rejected, 256));
+    if (!s->d_pa) AW_CUDA_TRY(aw_dev_malloc(&s->d_pa, sizeof(double) * 256));
     std::vector<uint8_t> rej(nw, 0);
     for (int i = 0; i < nw && i < (int)s->plane_rejected.size(); ++i) rej[i] = s->plane_rejected[i];
     AW_CUDA_TRY(cudaMemcpyAsync(s->d_rejected, rej.data(), nw, cudaMemcpyHostToDevice, st));

@@ -184,7 +184,9 @@ int check_frame(const aw_sky_frame *f, const char *name) {
     return AW_OK;
 }
 
-#define MO_GUARD_BEGIN try {
+#define MO_GUARD_BEGIN \
+    AW_TRACE();         \
+    try {
 #define MO_GUARD_END                                                   \
     }                                                                  \
     catch (const std::bad_alloc &) {                                   \

@@ -310,7 +310,7 @@ int grid_blocks(int64_t n, int threads) {
 
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    ~DevBuf() { if (p) aw_dev_free(p); }
 };
 
 int ilog2(int v) {
@@ -386,9 +386,9 @@ int build_items(const uint64_t *keys, int64_t nv, int shift, int chunk, const aw
     AW_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t nseg = (int64_t)last_id + last_flag;
     DevBuf bstarts, bnch, bbase;
-    AW_CUDA_TRY(cudaMalloc(&bstarts.p, sizeof(uint32_t) * nseg));
-    AW_CUDA_TRY(cudaMalloc(&bnch.p, sizeof(uint32_t) * nseg));
-    AW_CUDA_TRY(cudaMalloc(&bbase.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(aw_dev_malloc(&bstarts.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(aw_dev_malloc(&bnch.p, sizeof(uint32_t) * nseg));
+    AW_CUDA_TRY(aw_dev_malloc(&bbase.p, sizeof(uint32_t) * nseg));
     seg_start_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(flag, segid, nv, (uint32_t *)bstarts.p);
     AW_CHECK_LAUNCH();
     seg_chunks_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, nseg, (uint32_t)nv, chunk,
@@ -401,7 +401,7 @@ int build_items(const uint64_t *keys, int64_t nv, int shift, int chunk, const aw
     AW_CUDA_TRY(cudaMemcpyAsync(&ln, (uint32_t *)bnch.p + nseg - 1, 4, cudaMemcpyDeviceToHost, s));
     AW_CUDA_TRY(cudaStreamSynchronize(s));
     *nitems = (int64_t)lb + ln;
-    AW_CUDA_TRY(cudaMalloc(items, sizeof(int4) * std::max<int64_t>(*nitems, 1)));
+    AW_CUDA_TRY(aw_dev_malloc(items, sizeof(int4) * std::max<int64_t>(*nitems, 1)));
     emit_items_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, (uint32_t *)bbase.p, nseg,
                                                             (uint32_t)nv, chunk, rec, *items);
     AW_CHECK_LAUNCH();
@@ -443,15 +443,15 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     // per-plane supports first (the coordinate step indexes by w plane), then per bin
     std::vector<int32_t> sup(ks->supports.begin(), ks->supports.end());
     plan->bin_support = ks->bin_support;
-    AW_CUDA_TRY(cudaMalloc(&plan->d_plane_support, sizeof(int32_t) * std::max<size_t>(sup.size(), 1)));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_plane_support, sizeof(int32_t) * std::max<size_t>(sup.size(), 1)));
     AW_CUDA_TRY(cudaMemcpy(plan->d_plane_support, sup.data(), sizeof(int32_t) * sup.size(), cudaMemcpyHostToDevice));
-    AW_CUDA_TRY(cudaMalloc(&plan->d_wsum, sizeof(double)));
-    AW_CUDA_TRY(cudaMalloc(&plan->d_nonfinite, sizeof(unsigned long long)));
-    AW_CUDA_TRY(cudaMalloc(&plan->d_counter, sizeof(unsigned int) * 4));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_wsum, sizeof(double)));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_nonfinite, sizeof(unsigned long long)));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_counter, sizeof(unsigned int) * 4));
     const int64_t n = vis->nvis;
-    AW_CUDA_TRY(cudaMalloc(&plan->d_rec, sizeof(aw_rec) * std::max<int64_t>(n, 1)));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_rec, sizeof(aw_rec) * std::max<int64_t>(n, 1)));
     if (n == 0) {
-        AW_CUDA_TRY(cudaMalloc(&plan->d_items, sizeof(int4)));
+        AW_CUDA_TRY(aw_dev_malloc(&plan->d_items, sizeof(int4)));
         return AW_OK;
     }
     CoordArgs a;
@@ -467,12 +467,12 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     const int passes = (kbits + 1 + 7) / 8;
 
     DevBuf bk0, bk1, bv0, bv1, brec, bcnt, bcounts, bscan, bscratch;
-    AW_CUDA_TRY(cudaMalloc(&bk0.p, sizeof(uint64_t) * n));
-    AW_CUDA_TRY(cudaMalloc(&bk1.p, sizeof(uint64_t) * n));
-    AW_CUDA_TRY(cudaMalloc(&bv0.p, sizeof(uint32_t) * n));
-    AW_CUDA_TRY(cudaMalloc(&bv1.p, sizeof(uint32_t) * n));
-    AW_CUDA_TRY(cudaMalloc(&brec.p, sizeof(aw_rec) * n));
-    AW_CUDA_TRY(cudaMalloc(&bcnt.p, sizeof(unsigned long long) * 4));
+    AW_CUDA_TRY(aw_dev_malloc(&bk0.p, sizeof(uint64_t) * n));
+    AW_CUDA_TRY(aw_dev_malloc(&bk1.p, sizeof(uint64_t) * n));
+    AW_CUDA_TRY(aw_dev_malloc(&bv0.p, sizeof(uint32_t) * n));
+    AW_CUDA_TRY(aw_dev_malloc(&bv1.p, sizeof(uint32_t) * n));
+    AW_CUDA_TRY(aw_dev_malloc(&brec.p, sizeof(aw_rec) * n));
+    AW_CUDA_TRY(aw_dev_malloc(&bcnt.p, sizeof(unsigned long long) * 4));
     AW_CUDA_TRY(cudaMemsetAsync(bcnt.p, 0, sizeof(unsigned long long) * 4, s));
     uint64_t *k0 = (uint64_t *)bk0.p, *k1 = (uint64_t *)bk1.p;
     uint32_t *v0 = (uint32_t *)bv0.p, *v1 = (uint32_t *)bv1.p;
@@ -483,9 +483,9 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     const int64_t ncounts = (int64_t)256 * ntiles;
     const int64_t scan_n = std::max<int64_t>(ncounts, n + 1);
-    AW_CUDA_TRY(cudaMalloc(&bcounts.p, sizeof(uint32_t) * scan_n));
-    AW_CUDA_TRY(cudaMalloc(&bscan.p, sizeof(uint32_t) * scan_n));
-    AW_CUDA_TRY(cudaMalloc(&bscratch.p, aw_scan_scratch_bytes(scan_n)));
+    AW_CUDA_TRY(aw_dev_malloc(&bcounts.p, sizeof(uint32_t) * scan_n));
+    AW_CUDA_TRY(aw_dev_malloc(&bscan.p, sizeof(uint32_t) * scan_n));
+    AW_CUDA_TRY(aw_dev_malloc(&bscratch.p, aw_scan_scratch_bytes(scan_n)));
     uint32_t *counts = (uint32_t *)bcounts.p, *offs = (uint32_t *)bscan.p;
     int rc = radix_sort_pairs(k0, v0, k1, v1, n, passes, counts, offs, bscratch.p, s);
     if (rc) return rc;
@@ -500,7 +500,7 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     plan->mean_taps = hc[2] ? (double)hc[3] / (double)hc[2] : 0.0;
     const int64_t nv = plan->nvalid;
     if (nv == 0) {
-        AW_CUDA_TRY(cudaMalloc(&plan->d_items, sizeof(int4)));
+        AW_CUDA_TRY(aw_dev_malloc(&plan->d_items, sizeof(int4)));
         plan->nitems = 0;
         return AW_OK;
     }
@@ -521,7 +521,7 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     AW_CHECK_LAUNCH();
     rc = radix_sort_pairs(k0, v0, k1, v1, nv, (dg_bits + 7) / 8, counts, offs, bscratch.p, s);
     if (rc) return rc;
-    AW_CUDA_TRY(cudaMalloc(&plan->d_rec_dg, sizeof(aw_rec) * nv));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_rec_dg, sizeof(aw_rec) * nv));
     gather_rec_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(plan->d_rec, v0, nv, plan->d_rec_dg);
     AW_CHECK_LAUNCH();
     rc = build_items(k0, nv, 2 * stbits, AW_DG_CHUNK, plan->d_rec_dg, counts, offs, bscratch.p,

@@ -425,13 +425,13 @@ int aw_export_table(const void *src, float2 *dst, int64_t nblocks, int L, int P,
 
 int aw_table_absmax(const float2 *src, int64_t n, float *out_host, cudaStream_t s) {
     unsigned int *d = nullptr;
-    AW_CUDA_TRY(cudaMalloc(&d, sizeof(unsigned int)));
+    AW_CUDA_TRY(aw_dev_malloc(&d, sizeof(unsigned int)));
     cudaMemsetAsync(d, 0, sizeof(unsigned int), s);
     absmax_kernel<<<blocks_for(n, 256, 152 * 16), 256, 0, s>>>(src, n, d);
     unsigned int h = 0;
     cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    cudaFree(d);
+    aw_dev_free(d);
     if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "absmax: %s", cudaGetErrorString(e));
     unsigned int bits = h;
     float f;
@@ -525,9 +525,9 @@ int aw_kernel_set_geometry(const aw_kernel_spec *spec, aw_kernel_set *ks) {
 }
 
 int aw_kernel_set_alloc(aw_kernel_set *ks) {
-    AW_CUDA_TRY(cudaMalloc(&ks->d_table, (size_t)ks->total_elems * ks->elem_bytes));
-    AW_CUDA_TRY(cudaMalloc(&ks->d_bin_support, sizeof(int32_t) * ks->nbins));
-    AW_CUDA_TRY(cudaMalloc(&ks->d_bin_offset, sizeof(int64_t) * ks->nbins));
+    AW_CUDA_TRY(aw_dev_malloc(&ks->d_table, (size_t)ks->total_elems * ks->elem_bytes));
+    AW_CUDA_TRY(aw_dev_malloc(&ks->d_bin_support, sizeof(int32_t) * ks->nbins));
+    AW_CUDA_TRY(aw_dev_malloc(&ks->d_bin_offset, sizeof(int64_t) * ks->nbins));
     AW_CUDA_TRY(cudaMemcpy(ks->d_bin_support, ks->bin_support.data(), sizeof(int32_t) * ks->nbins,
                            cudaMemcpyHostToDevice));
     AW_CUDA_TRY(cudaMemcpy(ks->d_bin_offset, ks->bin_offset.data(), sizeof(int64_t) * ks->nbins,
@@ -552,13 +552,13 @@ int aw_synthesise(aw_ctx *ctx, aw_kernel_set *ks, cudaStream_t s) {
     unsigned long long *d_bmax = nullptr;
     int rc = AW_OK;
     auto cleanup = [&]() {
-        if (Z) cudaFree(Z);
-        if (d_taper) cudaFree(d_taper);
-        if (d_bmax) cudaFree(d_bmax);
+        if (Z) aw_dev_free(Z);
+        if (d_taper) aw_dev_free(d_taper);
+        if (d_bmax) aw_dev_free(d_bmax);
     };
-    cudaError_t e = cudaMalloc(&Z, zmax * sizeof(cufftDoubleComplex));
-    if (e == cudaSuccess) e = cudaMalloc(&d_taper, 256 * 64 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&d_bmax, 4 * sizeof(unsigned long long));
+    cudaError_t e = aw_dev_malloc(&Z, zmax * sizeof(cufftDoubleComplex));
+    if (e == cudaSuccess) e = aw_dev_malloc(&d_taper, 256 * 64 * sizeof(double));
+    if (e == cudaSuccess) e = aw_dev_malloc(&d_bmax, 4 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cleanup();
         return aw_set_error(AW_ENOMEM, "synthesis buffers: %s", cudaGetErrorString(e));
