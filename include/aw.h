@@ -703,6 +703,17 @@ int aw_clean(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kgrid, const aw_ke
  */
 int aw_debug_fail_alloc(int64_t n);
 int aw_debug_alloc_stats(int64_t *live, int64_t *calls);
+/*
+ * aw_debug_bounds_status - in a library built with -DAW_BOUNDS_CHECK, where
+ * the gridding and degridding kernels check every grid, table, shared-memory,
+ * record and output index (a bad one is skipped and recorded): *status = the
+ * code of the first failed check since the last reset, 0 if none (1-4 tile
+ * gridding: grid, table, shared memory, record; 5-8 the same for the offset
+ * schedule; 9-13 degridding: table source, shared-memory destination, grid,
+ * partial sums, record); reset != 0 clears it.  Synchronises the device.
+ * AW_EUNSUPPORTED in a normal build.
+ */
+int aw_debug_bounds_status(uint32_t *status, int32_t reset);
 int aw_debug_wait_timeout(aw_ctx *ctx, int32_t which, void *stream);
 
 #ifdef __cplusplus

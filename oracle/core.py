@@ -509,7 +509,8 @@ _lib = None
 def _c():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(_build.build())
+        import os
+        _lib = ctypes.CDLL(_build.build(sanitize=os.environ.get("AW_ORACLE_SANITIZE") == "1"))
         P = ctypes.c_void_p
         i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         _lib.oracle_coords.argtypes = [i64, P, P, P, P, P, P, P, i32, dbl, i32, i32, dbl,

@@ -12,7 +12,8 @@ import os
 from typing import Optional, Sequence
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libaw.so")
+# AW_LIBAW selects another build of the library (the bounds-checked one in its test)
+LIB_PATH = os.environ.get("AW_LIBAW") or os.path.join(HERE, "libaw.so")
 
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ETIMEOUT, AW_EUNSUPPORTED, AW_EREJECTED = range(7)
 AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT, AW_ROLE_BEAM = 0, 1, 2, 3
@@ -115,6 +116,7 @@ SIGNATURES = {
     "aw_debug_fail_alloc": (ctypes.c_int, [c_i64]),
     "aw_debug_alloc_stats": (ctypes.c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "aw_debug_wait_timeout": (ctypes.c_int, [c_p, c_i32, c_p]),
+    "aw_debug_bounds_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), c_i32]),
     "aw_degrid_learned": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_save": (ctypes.c_int, [c_p, ctypes.c_char_p]),
     "aw_surrogate_load": (ctypes.c_int, [c_p, ctypes.c_char_p, ctypes.POINTER(c_p)]),
@@ -605,3 +607,10 @@ def aw_debug_alloc_stats():
 def aw_debug_wait_timeout(ctx: Handle, which: int, stream=None) -> int:
     """Status code of the bounded-wait self-test (AW_ETIMEOUT is the expected outcome)."""
     return int(load().aw_debug_wait_timeout(ctx.ptr, int(which), _stream(stream)))
+
+
+def aw_debug_bounds_status(reset: bool = False) -> int:
+    """Code of the first failed bounds check (0: none); raises in a build without the checks."""
+    st = ctypes.c_uint32()
+    _check(load().aw_debug_bounds_status(ctypes.byref(st), int(bool(reset))), "aw_debug_bounds_status")
+    return st.value

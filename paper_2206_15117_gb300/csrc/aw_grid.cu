@@ -24,7 +24,32 @@
 
 #include "aw_internal.h"
 
+// Debug builds with -DAW_BOUNDS_CHECK check every grid, table, shared-memory,
+// record and output index of the kernels in this file: a bad index records a
+// code in a device status word (the first one wins) and the access is
+// skipped.  Normal builds compile the checks away.
+#ifdef AW_BOUNDS_CHECK
+__device__ unsigned int g_bounds_status;
+#endif
+
 namespace {
+
+#ifdef AW_BOUNDS_CHECK
+__device__ __forceinline__ bool bounds_ok(bool ok, unsigned int code) {
+    if (!ok) atomicCAS(&g_bounds_status, 0u, code);
+    return ok;
+}
+#define AW_BOK(cond, code) bounds_ok((cond), (code))
+#else
+#define AW_BOK(cond, code) true
+#endif
+
+// codes of the bounds checks
+enum : unsigned int {
+    BC_T_GRID = 1, BC_T_TAB, BC_T_SMEM, BC_T_REC,        // tile schedule
+    BC_O_GRID = 5, BC_O_TAB, BC_O_SMEM, BC_O_REC,        // offset schedule
+    BC_D_SRC = 9, BC_D_DST, BC_D_GRID, BC_D_OUT, BC_D_REC  // degridding
+};
 
 template <int ST>
 struct KTraits;
@@ -113,6 +138,7 @@ struct GridArgs {
     unsigned long long *nonfinite;
     unsigned int *counter;   // persistent queue head
     float inv_scale;         // 1 / table scale
+    int64_t nvis, nvalid, tab_elems;  // extents for the bounds checks
 };
 
 template <int NPOL>
@@ -137,7 +163,9 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
     double wloc = 0.0;
     unsigned long long nbad = 0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        if (!AW_BOK(i < a.chunk && start + i < a.nvalid, BC_T_SMEM)) continue;
         const aw_rec r = a.rec[start + i];
+        if (!AW_BOK(r.orig < a.nvis, BC_T_REC)) continue;
         float2 v[NPOL];
         float w[NPOL];
         bool bad = false;
@@ -201,6 +229,7 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
 #pragma unroll
             for (int s = 0; s < NPOL; ++s) acc[s] = make_float2(0.f, 0.f);
             for (int i = g; i < count; i += G) {
+                if (!AW_BOK(i < a.chunk, BC_T_SMEM)) break;
                 const int4 meta = s_meta[i];
                 const int pos = meta.x;
                 const int md = meta.y;
@@ -214,15 +243,19 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
                 if (key != cur) {
                     if (cur >= 0) {
                         const int cx = cur & 0xffff, cy = cur >> 16;
+                        if (AW_BOK(cx < a.N && cy < a.N, BC_T_GRID))
 #pragma unroll
-                        for (int s = 0; s < NPOL; ++s)
-                            atomicAdd(a.grid + ((int64_t)s * a.N + cy) * a.N + cx, acc[s]);
+                            for (int s = 0; s < NPOL; ++s)
+                                atomicAdd(a.grid + ((int64_t)s * a.N + cy) * a.N + cx, acc[s]);
                     }
                     cur = key;
 #pragma unroll
                     for (int s = 0; s < NPOL; ++s) acc[s] = make_float2(0.f, 0.f);
                 }
                 float2 k[P];
+                if (!AW_BOK(meta.z >= 0 && tab0 + meta.z + (int64_t)P * L <= a.tab_elems && jy * S + jx < L,
+                            BC_T_TAB))
+                    continue;
                 load_k<ST, P>(a.ktab, tab0 + meta.z, L, jy * S + jx, k);
                 float2 v[NPOL];
                 if constexpr (NPOL == 4) {
@@ -240,9 +273,10 @@ __device__ __forceinline__ void grid_one_item(const GridArgs &a, int item, char 
             }
             if (cur >= 0) {
                 const int cx = cur & 0xffff, cy = cur >> 16;
+                if (AW_BOK(cx < a.N && cy < a.N, BC_T_GRID))
 #pragma unroll
-                for (int s = 0; s < NPOL; ++s)
-                    atomicAdd(a.grid + ((int64_t)s * a.N + cy) * a.N + cx, acc[s]);
+                    for (int s = 0; s < NPOL; ++s)
+                        atomicAdd(a.grid + ((int64_t)s * a.N + cy) * a.N + cx, acc[s]);
             }
         }
     }
@@ -293,6 +327,7 @@ struct GridOffArgs {
     double *wsum;
     unsigned long long *nonfinite;
     float inv_scale;
+    int64_t nvis, nvalid, tab_elems;  // extents for the bounds checks
 };
 
 __host__ __device__ inline int gcd_i(int a, int b) {
@@ -317,15 +352,17 @@ __global__ void __launch_bounds__(256) grid_offset_kernel(GridOffArgs a) {
         const int L = S * S;
         const float invS = 1.0f / (float)S;
         __syncthreads();  // the previous item has finished with s_v / s_pos
-        if ((int)threadIdx.x < count) {
+        if ((int)threadIdx.x < count && AW_BOK(count <= AW_DG_CHUNK && start + (int)threadIdx.x < a.nvalid, BC_O_SMEM)) {
             const aw_rec r = a.rec_dg[start + threadIdx.x];
+            // (checked builds: a bad record reads visibility 0 instead)
+            const int64_t orig = AW_BOK(r.orig < a.nvis, BC_O_REC) ? (int64_t)r.orig : 0;
             float2 v[NPOL];
             float w[NPOL];
             bool bad = false;
 #pragma unroll
             for (int c = 0; c < NPOL; ++c) {
-                v[c] = a.vis[(int64_t)r.orig * NPOL + c];
-                w[c] = a.weight ? a.weight[(int64_t)r.orig * NPOL + c] : 1.0f;
+                v[c] = a.vis[orig * NPOL + c];
+                w[c] = a.weight ? a.weight[orig * NPOL + c] : 1.0f;
                 bad |= !isfinite(v[c].x) || !isfinite(v[c].y) || !isfinite(w[c]);
             }
             if (r.flip) {
@@ -361,8 +398,9 @@ __global__ void __launch_bounds__(256) grid_offset_kernel(GridOffArgs a) {
             const int jy = (int)(((float)t + 0.5f) * invS);
             const int jx = t - jy * S;
             float2 k[P];
+            if (!AW_BOK(kbase >= 0 && kbase + (int64_t)P * L <= a.tab_elems, BC_O_TAB)) continue;
             load_k<ST, P>(a.ktab, kbase, L, t, k);
-            for (int j = p; j < count; j += nsplit) {
+            for (int j = p; j < count && AW_BOK(j < AW_DG_CHUNK, BC_O_SMEM); j += nsplit) {
                 float2 v[NPOL];
                 if constexpr (NPOL == 4) {
                     const float4 v01 = reinterpret_cast<const float4 *>(s_v)[2 * j];
@@ -373,6 +411,7 @@ __global__ void __launch_bounds__(256) grid_offset_kernel(GridOffArgs a) {
                     v[0] = s_v[j];
                 }
                 const int2 pos = s_pos[j];
+                if (!AW_BOK(pos.x >= 0 && pos.y >= 0 && pos.x + jx < a.N && pos.y + jy < a.N, BC_O_GRID)) continue;
                 float2 *dst = a.grid + (int64_t)(pos.y + jy) * a.N + (pos.x + jx);
 #pragma unroll
                 for (int s = 0; s < NPOL; ++s) {
@@ -415,6 +454,7 @@ struct DegridArgs {
     const float2 *sub_from;  // if set: vis_out = sub_from - prediction (may alias vis_out)
     int N, OS;
     float inv_scale;
+    int64_t tab_elems;       // table extent for the bounds checks
 };
 
 constexpr int DG_TS = 256;  // taps per shared-memory slab of the kernel block
@@ -531,8 +571,10 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
         const uint32_t dst = smem_u32(dsm) + (uint32_t)(b * TC::SLAB_BYTES);
         for (int idx = threadIdx.x; idx < ns * TC::NCH; idx += blockDim.x) {
             const int c = idx / ns, tl = idx - c * ns;
-            cp_async_chunk<TC::CB>(dst + (uint32_t)((c * DG_TS + tl) * TC::CB),
-                                   src + ((int64_t)c * L + t0 + tl) * TC::CB);
+            if (AW_BOK(kbase >= 0 && kbase + ((int64_t)c * L + t0 + tl + 1) * TC::CE <= a.tab_elems, BC_D_SRC) &&
+                AW_BOK(c < TC::NCH && tl < DG_TS, BC_D_DST))
+                cp_async_chunk<TC::CB>(dst + (uint32_t)((c * DG_TS + tl) * TC::CB),
+                                       src + ((int64_t)c * L + t0 + tl) * TC::CB);
         }
         cp_async_commit();
     };
@@ -567,12 +609,15 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
                 for (int j = 0; j < VB; ++j) {
                     const int v = g + ngp * j;
                     has[j] = v < count;
-                    const aw_rec r = a.rec_dg[start + (has[j] ? v : 0)];
+                    const bool inr = AW_BOK(start + (has[j] ? v : 0) < a.nvalid, BC_D_REC);
+                    has[j] = has[j] && inr;
+                    const aw_rec r = a.rec_dg[inr ? start + (has[j] ? v : 0) : 0];
                     goff[j] = (uint32_t)r.y0 * (uint32_t)a.N + r.x0;
                 }
 #pragma unroll
                 for (int i = 0; i < NV; ++i) acc[i] = 0.f;
-                for (int i = threadIdx.x; i < count * NPOL * 2; i += blockDim.x) s_out[i] = 0.f;
+                for (int i = threadIdx.x; i < count * NPOL * 2; i += blockDim.x)
+                    if (AW_BOK(i < AW_DG_CHUNK * NPOL * 2, BC_D_OUT)) s_out[i] = 0.f;
             }
             // the next (item, slab) streams into the other buffer
             int64_t nitem = item;
@@ -598,7 +643,9 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
                 for (int j = 0; j < VB; ++j) {
 #pragma unroll
                     for (int s2 = 0; s2 < NPOL; ++s2)
-                        gv[j][s2] = has[j] ? __ldg(gplane[s2] + (goff[j] + toff)) : make_float2(0.f, 0.f);
+                        gv[j][s2] = (has[j] && AW_BOK(goff[j] + toff < (uint32_t)a.N * (uint32_t)a.N, BC_D_GRID))
+                                        ? __ldg(gplane[s2] + (goff[j] + toff))
+                                        : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int c = 0; c < NPOL; ++c) {
@@ -624,7 +671,8 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
                 if constexpr (NV == 32) {
                     reduce_scatter_step<16>(acc, lane);
                     const int j = lane / (NPOL * 2), v = g + ngp * j;
-                    if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (lane % (NPOL * 2))], acc[0]);
+                    if (v < count && AW_BOK(v < AW_DG_CHUNK, BC_D_OUT))
+                        atomicAdd(&s_out[v * NPOL * 2 + (lane % (NPOL * 2))], acc[0]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < NV; ++i)
@@ -633,13 +681,16 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
 #pragma unroll
                         for (int i = 0; i < NV; ++i) {
                             const int j = i / (NPOL * 2), v = g + ngp * j;
-                            if (v < count) atomicAdd(&s_out[v * NPOL * 2 + (i % (NPOL * 2))], acc[i]);
+                            if (v < count && AW_BOK(v < AW_DG_CHUNK, BC_D_OUT))
+                                atomicAdd(&s_out[v * NPOL * 2 + (i % (NPOL * 2))], acc[i]);
                         }
                     }
                 }
                 __syncthreads();
                 for (int v = threadIdx.x; v < count; v += blockDim.x) {
+                    if (!AW_BOK(v < AW_DG_CHUNK && start + v < a.nvalid, BC_D_REC)) continue;
                     const aw_rec r = a.rec_dg[start + v];
+                    if (!AW_BOK(r.orig < a.nvis, BC_D_REC)) continue;
                     float2 out[NPOL];
 #pragma unroll
                     for (int c = 0; c < NPOL; ++c)
@@ -757,6 +808,9 @@ int launch_grid_offsets(const aw_grid_launch &L) {
     a.wsum = p->d_wsum;
     a.nonfinite = p->d_nonfinite;
     a.inv_scale = 1.0f / k->scale;
+    a.nvis = p->nvis;
+    a.nvalid = p->nvalid;
+    a.tab_elems = k->total_elems;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -795,6 +849,9 @@ int aw_launch_grid(const aw_grid_launch &L) {
     a.nonfinite = p->d_nonfinite;
     a.counter = p->d_counter;
     a.inv_scale = 1.0f / k->scale;
+    a.nvis = p->nvis;
+    a.nvalid = p->nvalid;
+    a.tab_elems = k->total_elems;
     const int st = k->spec.storage;
     if (p->npol == 1) {
         if (st == AW_STORAGE_FP32) return launch_grid_t<1, AW_STORAGE_FP32>(L, a);
@@ -825,6 +882,7 @@ int aw_launch_degrid(const aw_plan *p, const aw_kernel_set *k, const void *grid,
     a.N = p->N;
     a.OS = p->OS;
     a.inv_scale = 1.0f / k->scale;
+    a.tab_elems = k->total_elems;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -837,4 +895,25 @@ int aw_launch_degrid(const aw_plan *p, const aw_kernel_set *k, const void *grid,
     if (st == AW_STORAGE_FP32) return launch_degrid_t<4, AW_STORAGE_FP32>(a, sms, s);
     if (st == AW_STORAGE_BF16) return launch_degrid_t<4, AW_STORAGE_BF16>(a, sms, s);
     return launch_degrid_t<4, AW_STORAGE_FP16>(a, sms, s);
+}
+
+// Bounds-check status of the kernels in this file: AW_EUNSUPPORTED unless the
+// library was built with -DAW_BOUNDS_CHECK.
+extern "C" int aw_debug_bounds_status(uint32_t *status, int32_t reset) {
+    if (!status) return aw_set_error(AW_EINVAL, "status is NULL");
+#ifdef AW_BOUNDS_CHECK
+    unsigned int v = 0;
+    AW_CUDA_TRY(cudaDeviceSynchronize());
+    AW_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_bounds_status, sizeof(v)));
+    if (reset) {
+        const unsigned int z = 0;
+        AW_CUDA_TRY(cudaMemcpyToSymbol(g_bounds_status, &z, sizeof(z)));
+    }
+    *status = v;
+    return AW_OK;
+#else
+    (void)reset;
+    *status = 0;
+    return aw_set_error(AW_EUNSUPPORTED, "built without AW_BOUNDS_CHECK");
+#endif
 }
