@@ -856,6 +856,12 @@ def run_ours(args, rank, world, dist):
     grid = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
     image = torch.empty((4, N, N), dtype=torch.float32, device=dev)
     launches_per_step = 4   # grid (persistent), checker + grid-correction (FFT step), degrid
+    # pinned host buffers of the end-to-end measurement, allocated up front: allocated after the
+    # BF16/FP16 variant sets had been built and freed, the same transfers measured about 9x slower
+    host_bufs = None
+    if not args.no_e2e:
+        host_bufs = (torch.empty((nvis, 4), dtype=torch.complex64, pin_memory=True),
+                     torch.empty((nvis, 4), dtype=torch.complex64, pin_memory=True))
 
     def step(ev=None, kset_g=kg, kset_d=kd):
         grid.zero_()
@@ -941,9 +947,8 @@ def run_ours(args, rank, world, dist):
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
-        vis_host = torch.empty((nvis, 4), dtype=torch.complex64, pin_memory=True)
+        vis_host, out_host = host_bufs
         vis_host.copy_(vis)
-        out_host = torch.empty((nvis, 4), dtype=torch.complex64, pin_memory=True)
         vis_dev = torch.empty_like(vis)
         ne = max(3, min(args.steps, 6))
 
