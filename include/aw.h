@@ -229,6 +229,24 @@ int aw_kernel_set_import(aw_ctx *ctx, const aw_kernel_spec *spec, const void *ta
  * device memory `dst` ([OS][OS][S][S][P] complex64). */
 int aw_kernel_set_export(const aw_kernel_set *kset, int32_t bin, void *dst, void *stream);
 int aw_kernel_set_info(const aw_kernel_set *kset, aw_kernel_info *info);
+
+/*
+ * Kernel-set cache on disk.  aw_kernel_spec_hash - a 64-bit key of `spec`:
+ * FNV-1a 64 of a canonical little-endian encoding of the spec after the
+ * library's own validation and normalisation (every field and array that
+ * defines the tables; AW_EINVAL for an invalid spec).  aw_kernel_set_save -
+ * write `kset` to `path`: magic "AWKSET01", that spec encoding, the table
+ * scale, the rejected-bin count and the table size, a header checksum, then
+ * the tables in their storage format and layout and a checksum of them
+ * (streamed through host memory in 256 MiB pieces; synchronises the device).
+ * aw_kernel_set_load - a new set on ctx's device from such a file (*out, freed
+ * with aw_kernel_set_destroy): the same geometry, tables and scale.  AW_EINVAL
+ * (and *out = NULL) if the file is missing, truncated, has trailing bytes, a
+ * bad magic or checksum, or tables whose size does not match its spec.
+ */
+int aw_kernel_spec_hash(const aw_kernel_spec *spec, uint64_t *hash);
+int aw_kernel_set_save(const aw_kernel_set *kset, const char *path);
+int aw_kernel_set_load(aw_ctx *ctx, const char *path, aw_kernel_set **out);
 int aw_kernel_set_destroy(aw_kernel_set *kset);
 
 /* ---- plan: coordinates (FP64) and device key sort --------------------------- */

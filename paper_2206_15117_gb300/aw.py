@@ -119,6 +119,9 @@ SIGNATURES = {
     "aw_debug_bounds_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), c_i32]),
     "aw_degrid_learned": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_save": (ctypes.c_int, [c_p, ctypes.c_char_p]),
+    "aw_kernel_spec_hash": (ctypes.c_int, [ctypes.POINTER(aw_kernel_spec), ctypes.POINTER(ctypes.c_uint64)]),
+    "aw_kernel_set_save": (ctypes.c_int, [c_p, ctypes.c_char_p]),
+    "aw_kernel_set_load": (ctypes.c_int, [c_p, ctypes.c_char_p, ctypes.POINTER(c_p)]),
     "aw_surrogate_load": (ctypes.c_int, [c_p, ctypes.c_char_p, ctypes.POINTER(c_p)]),
     "aw_reproject": (ctypes.c_int, [c_p, c_p, ctypes.POINTER(aw_sky_frame), c_p, ctypes.POINTER(aw_sky_frame),
                                     c_i32, c_i32, ctypes.c_float, c_p]),
@@ -306,6 +309,37 @@ def aw_kernel_set_info(kset: Handle) -> aw_kernel_info:
 
 def aw_kernel_set_export(kset: Handle, b: int, dst, stream=None):
     _check(load().aw_kernel_set_export(kset.ptr, int(b), _ptr(dst), _stream(stream)), "aw_kernel_set_export")
+
+
+def aw_kernel_spec_hash(**spec_kw) -> int:
+    spec, keep = make_spec(**spec_kw)
+    h = ctypes.c_uint64()
+    _check(load().aw_kernel_spec_hash(ctypes.byref(spec), ctypes.byref(h)), "aw_kernel_spec_hash")
+    return h.value
+
+
+def aw_kernel_set_save(kset: Handle, path: str):
+    _check(load().aw_kernel_set_save(kset.ptr, os.fsencode(path)), "aw_kernel_set_save")
+
+
+def aw_kernel_set_load(ctx: Handle, path: str) -> Handle:
+    out = c_p()
+    _check(load().aw_kernel_set_load(ctx.ptr, os.fsencode(path), ctypes.byref(out)), "aw_kernel_set_load")
+    return Handle(out, "aw_kernel_set_destroy")
+
+
+def cached_kernels(ctx: Handle, cache_dir: str, **spec_kw) -> Handle:
+    """aw_make_kernels through an on-disk cache keyed by aw_kernel_spec_hash."""
+    key = aw_kernel_spec_hash(**spec_kw)
+    path = os.path.join(cache_dir, "awkset-%016x.bin" % key)
+    if os.path.exists(path):
+        return aw_kernel_set_load(ctx, path)
+    ks = aw_make_kernels(ctx, **spec_kw)
+    os.makedirs(cache_dir, exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    aw_kernel_set_save(ks, tmp)
+    os.replace(tmp, path)
+    return ks
 
 
 def aw_kernel_set_destroy(kset: Handle):
