@@ -947,13 +947,18 @@ def run_ours(args, rank, world, dist):
     achieved = flops / (dom_ms / 1e3) / 1e12
     # DRAM bytes per launch of the dominant kernel, from the one-pass ncu capture summarised in
     # profiles/dram_traffic_fullpol_aw_64M.md (same kernels, this workload, FP32 tables); null otherwise
-    # (the tile schedule depends on tile and chunk, the offset-grouped kernels on the super-tile)
+    # (the tile schedule depends on tile and chunk, the offset-grouped gridder on the super-tile and
+    # the CTAs in flight, the degridder on the super-tile)
     measured_traffic = {("grid_persistent_kernel", 63851035, 64, 128): 149.65e9,
-                        ("grid_offset_kernel", 63851035, 1024): 49.03e9,
-                        ("degrid_items_kernel", 63851035, 1024): 14.71e9}
+                        ("grid_offset_kernel", 63851035, 1024, 5): 40.72e9,
+                        ("degrid_items_kernel", 63851035, 1024): 14.43e9}
     kname = gname if g_ms >= d_ms else "degrid_items_kernel"
-    dom_kernel = ((kname, int(nvis), tune.tile, tune.chunk) if kname == "grid_persistent_kernel"
-                  else (kname, int(nvis), tune.dg_tile or 1024))
+    if kname == "grid_persistent_kernel":
+        dom_kernel = (kname, int(nvis), tune.tile, tune.chunk)
+    elif kname == "grid_offset_kernel":
+        dom_kernel = (kname, int(nvis), tune.dg_tile or 1024, tune.ctas_per_sm)
+    else:
+        dom_kernel = (kname, int(nvis), tune.dg_tile or 1024)
     traffic = measured_traffic.get(dom_kernel) if not args.subset else None
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic,
