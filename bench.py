@@ -80,10 +80,8 @@ def workload(time_samples: int, subset: bool = False):
                                "pa_centres": ob.pa_centres[a:a + 1], "fbin_freqs": ob.fbin_freqs[f:f + 1]})
     g = sy.grid_geometry(3)
     nw = 32
-    kw = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=7.0, npol=4, nw=nw, w_max=ob.w_max,
-              supports=sy.w_supports(nw, extra=8), pa=list(ob.pa_centres),
-              fbin_freqs=list(ob.fbin_freqs), dish_d=12.0, d_xy=0.01 * np.exp(0.4j),
-              d_yx=0.01 * np.exp(-1.3j), eps=0.2)
+    kw = sy.config_spec(3, ob)
+    assert kw["nw"] == nw and kw["N"] == g["N"]
     return ob, kw
 
 
@@ -593,9 +591,7 @@ def learned_section(ctx, dev, args):
     stream = torch.cuda.current_stream()
     ob = sy.observation(5, field=0)
     g = sy.grid_geometry(5)
-    kw = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=7.0, npol=4, nw=32, w_max=ob.w_max,
-              supports=sy.w_supports(32), pa=list(ob.pa_centres), fbin_freqs=list(ob.fbin_freqs), dish_d=12.0,
-              d_xy=0.01 * np.exp(0.4j), d_yx=0.01 * np.exp(-1.3j), eps=0.2)
+    kw = sy.config_spec(5, ob)
     t0 = time.perf_counter()
     exact = aw.aw_make_kernels(ctx, **kw)
     t_synth = time.perf_counter() - t0

@@ -220,6 +220,32 @@ def grid_geometry(cfg: int) -> Dict:
     raise ValueError(cfg)
 
 
+# leakage of the configurations' feeds: 1 % with fixed phases
+LEAK_XY, LEAK_YX = 0.01 * complex(math.cos(0.4), math.sin(0.4)), 0.01 * complex(math.cos(-1.3), math.sin(-1.3))
+
+
+def config_spec(cfg: int, ob: "Observation") -> Dict:
+    """Kernel-set arguments (the fields of aw_kernel_spec) of configuration
+    `cfg` for its observation `ob`:
+      1: Stokes I, no w or A term, 7-cell PSWF kernel, OS 4, 512^2;
+      2, 4: Stokes I w-projection, 32 planes, supports 8..64, OS 8, 2048^2
+         (4 is 2 with BF16 / FP16 tables: pass storage separately);
+      3: full-pol AW, 32 planes, supports 16..72, the observation's PA and
+         beam-frequency bins, 12 m Airy beam, 1 % leakage, eps 0.2, 4096^2;
+      5: full-pol AW of one mosaic field, 32 planes, supports 8..64, 2048^2."""
+    g = grid_geometry(cfg)
+    base = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=g["W"])
+    if cfg == 1:
+        return dict(base, npol=1, nw=1, supports=[7])
+    if cfg in (2, 4):
+        return dict(base, npol=1, nw=32, w_max=ob.w_max, supports=w_supports(32))
+    if cfg in (3, 5):
+        return dict(base, npol=4, nw=32, w_max=ob.w_max, supports=w_supports(32, extra=8 if cfg == 3 else 0),
+                    pa=list(ob.pa_centres), fbin_freqs=list(ob.fbin_freqs), dish_d=12.0, d_xy=LEAK_XY,
+                    d_yx=LEAK_YX, eps=0.2)
+    raise ValueError(cfg)
+
+
 def w_supports(nw: int, extra: int = 0) -> List[int]:
     """Full kernel width per w plane: S_p = 8 max(1, round(8 w_p / w_max)) + extra,
     w_p = (p + 1/2) w_max / nw (8..64 cells for 32 planes; +8 for AW)."""

@@ -23,9 +23,7 @@ def rel_err(a, b):
 def case_stokes_i_cfg1(time_samples=200):
     """Configuration 1 geometry (36 antennas, 1 channel, 512^2, 7x7 PSWF, OS 4)."""
     ob = sy.observation(1, time_samples=time_samples)
-    g = sy.grid_geometry(1)
-    kw = dict(N=g["N"], dl=g["dl"], OS=g["OS"], W=7.0, npol=1, nw=1, supports=[7])
-    return ob, kw
+    return ob, sy.config_spec(1, ob)
 
 
 def case_wproj(vis_fraction=0.002, nw=32, N=2048):
