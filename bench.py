@@ -1014,39 +1014,44 @@ def run_ours(args, rank, world, dist):
                    "compute_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in pev),
                    "d2h_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in pev),
                    "serial_ms_per_step": e_ms_serial}
-        # the same steps pipelined: step k+1's visibilities are copied in on their own stream
-        # once step k's gridding has read the buffer (under its FFT and degridding), and step
-        # k's predictions are copied out on a third stream under step k+1's gridding
+        # the same steps pipelined over two device buffers of visibilities and of
+        # predictions: step k+1's visibilities are copied in on their own stream during step k
+        # (into the buffer step k-1 gridded from), and step k's predictions are copied out on
+        # a third stream during step k+1 (step k+2 reuses that buffer after the copy)
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in, ev_grid, ev_done, ev_out = (torch.cuda.Event() for _ in range(4))
+        vis_b = [vis_dev, torch.empty_like(vis)]
+        out_b = [vis_out, torch.empty_like(vis_out)]
+        ev_in, ev_grid, ev_done, ev_out = ([torch.cuda.Event(), torch.cuda.Event()] for _ in range(4))
 
         def pipelined(n):
             s_in.wait_stream(stream)
             with torch.cuda.stream(s_in):
-                vis_dev.copy_(vis_host, non_blocking=True)
-            ev_in.record(s_in)
+                vis_b[0].copy_(vis_host, non_blocking=True)
+            ev_in[0].record(s_in)
             for k in range(n):
-                stream.wait_event(ev_in)
-                grid.zero_()
-                aw.aw_grid_batched(ctx, plan, kg, vis_dev, None, grid)
-                ev_grid.record(stream)
+                b = k % 2
                 if k + 1 < n:
-                    s_in.wait_event(ev_grid)
+                    if k >= 1:
+                        s_in.wait_event(ev_grid[1 - b])   # step k-1 has gridded from that buffer
                     with torch.cuda.stream(s_in):
-                        vis_dev.copy_(vis_host, non_blocking=True)
-                    ev_in.record(s_in)
+                        vis_b[1 - b].copy_(vis_host, non_blocking=True)
+                    ev_in[1 - b].record(s_in)
+                stream.wait_event(ev_in[b])
+                grid.zero_()
+                aw.aw_grid_batched(ctx, plan, kg, vis_b[b], None, grid)
+                ev_grid[b].record(stream)
                 aw.aw_fft_to_image(ctx, kg, grid, float(info.nvalid), image)
-                if k > 0:
-                    stream.wait_event(ev_out)      # step k-1's predictions have left the device
-                aw.aw_degrid(ctx, plan, kd, model, vis_out)
-                ev_done.record(stream)
-                s_out.wait_event(ev_done)
+                if k >= 2:
+                    stream.wait_event(ev_out[b])      # step k-2's predictions have left that buffer
+                aw.aw_degrid(ctx, plan, kd, model, out_b[b])
+                ev_done[b].record(stream)
+                s_out.wait_event(ev_done[b])
                 with torch.cuda.stream(s_out):
-                    out_host.copy_(vis_out, non_blocking=True)
-                ev_out.record(s_out)
-            stream.wait_event(ev_out)
+                    out_host.copy_(out_b[b], non_blocking=True)
+                ev_out[b].record(s_out)
+            stream.wait_stream(s_out)
 
-        pipelined(1)
+        pipelined(2)     # also captures the gridding graph of each buffer
         torch.cuda.synchronize()
         a.record(stream)
         pipelined(ne)
@@ -1057,8 +1062,10 @@ def run_ours(args, rank, world, dist):
         e2e = {"value": world * nvis / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(nbytes),
                "d2h_bytes_per_step": int(nbytes), "ms_per_step": e_ms, "parts": e_parts,
                "how": "every step: pinned host visibilities copied in, grid + FFT + degrid, predicted visibilities "
-                      "copied out; copies on their own streams, overlapped with the neighbouring steps' compute "
-                      "(parts: the same steps run serially)"}
+                      "copied out; two device buffers each way, copies on their own streams overlapped with the "
+                      "neighbouring steps' compute (parts: the same steps run serially)"}
+        del pipelined, vis_b, out_b
+        torch.cuda.empty_cache()
 
     clean = None
     if not args.no_clean and not args.subset:

@@ -322,8 +322,10 @@ int aw_degrid(aw_ctx *ctx, const aw_plan *plan, const aw_kernel_set *kset, const
  * aw_grid_batched - aw_grid as one launch over all the plan's work items
  * (every channel, polarisation and w plane of uneven counts in one launch),
  * captured once in a CUDA graph and replayed.  With grid_mode TILES the
- * launch is persistent over a work queue, ctas_per_sm from the plan's tune.  The graph is cached in the plan for the last (vis, weight,
- * grid, kset) pointers; do not call it for one plan from two threads.
+ * launch is persistent over a work queue, ctas_per_sm from the plan's tune.
+ * The plan caches the graphs of the last two (vis, weight, grid, kset,
+ * stream) argument sets (a double-buffered caller alternates between two
+ * without re-capturing); do not call it for one plan from two threads.
  * Same result as aw_grid within FP32 summation-order rounding.
  */
 int aw_grid_batched(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kset, const void *vis,

@@ -222,7 +222,7 @@ int aw_kernel_set_destroy(aw_kernel_set *k) {
 
 static void free_plan(aw_plan *p) {
     if (!p) return;
-    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->drop_graphs();
     if (p->d_rec) aw_dev_free(p->d_rec);
     if (p->d_items) aw_dev_free(p->d_items);
     if (p->d_rec_dg) aw_dev_free(p->d_rec_dg);
@@ -364,10 +364,12 @@ int aw_grid_batched(aw_ctx *ctx, aw_plan *p, const aw_kernel_set *k, const void 
         if (stats) return fill_stats(p, stats, s);
         return AW_OK;
     }
-    const bool same = p->graph && p->g_vis == vis && p->g_weight == weight && p->g_grid == grid &&
-                      p->g_kset == k && p->g_stream == s;
-    if (!same) {
-        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+    aw_plan::GraphSlot *slot = nullptr;
+    for (auto &g : p->gslots)
+        if (g.exec && g.vis == vis && g.weight == weight && g.grid == grid && g.kset == k && g.stream == s) slot = &g;
+    if (!slot) {
+        slot = p->gslots[0].used <= p->gslots[1].used ? &p->gslots[0] : &p->gslots[1];
+        if (slot->exec) { cudaGraphExecDestroy(slot->exec); *slot = aw_plan::GraphSlot{}; }
         cudaStream_t cap;
         AW_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
@@ -382,18 +384,19 @@ int aw_grid_batched(aw_ctx *ctx, aw_plan *p, const aw_kernel_set *k, const void 
             rc = aw_launch_grid(L);
             e = cudaStreamEndCapture(cap, &g);
         }
-        if (e == cudaSuccess && rc == AW_OK) e = cudaGraphInstantiate(&p->graph, g, 0);
+        if (e == cudaSuccess && rc == AW_OK) e = cudaGraphInstantiate(&slot->exec, g, 0);
         if (g) cudaGraphDestroy(g);
         cudaStreamDestroy(cap);
         if (rc) return rc;
         if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        p->g_vis = vis;
-        p->g_weight = weight;
-        p->g_grid = grid;
-        p->g_kset = k;
-        p->g_stream = s;
+        slot->vis = vis;
+        slot->weight = weight;
+        slot->grid = grid;
+        slot->kset = k;
+        slot->stream = s;
     }
-    AW_CUDA_TRY(cudaGraphLaunch(p->graph, s));
+    slot->used = ++p->gclock;
+    AW_CUDA_TRY(cudaGraphLaunch(slot->exec, s));
     if (stats) return fill_stats(p, stats, s);
     return AW_OK;
     AW_GUARD_END
@@ -421,7 +424,7 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
     aw_tune bt{32, 256, 2, 0, AW_GRID_TILES};
     // one timing of aw_grid_batched on plan p: best of reps 2..3
     auto time_plan = [&](aw_plan *p, float *ms_out) -> int {
-        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        p->drop_graphs();
         float ms_best = 1e30f;
         int r = AW_OK;
         for (int rep = 0; rep < 3 && r == AW_OK; ++rep) {

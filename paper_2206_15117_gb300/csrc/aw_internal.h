@@ -139,10 +139,22 @@ struct aw_plan {
     // coordinate inputs kept for aw_plan_coords
     aw_vis_desc vis{};
     double uscale = 0, half = 0, winv = 0;
-    // cached graph for aw_grid_batched
-    cudaGraphExec_t graph = nullptr;
-    const void *g_vis = nullptr, *g_weight = nullptr, *g_grid = nullptr, *g_kset = nullptr;
-    cudaStream_t g_stream = nullptr;
+    // graphs of aw_grid_batched for the last two argument sets (double-buffered
+    // callers alternate between two), least recently used replaced first
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const void *vis = nullptr, *weight = nullptr, *grid = nullptr, *kset = nullptr;
+        cudaStream_t stream = nullptr;
+        uint64_t used = 0;
+    };
+    GraphSlot gslots[2];
+    uint64_t gclock = 0;
+    void drop_graphs() {
+        for (auto &g : gslots) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = GraphSlot{};
+        }
+    }
 };
 
 // Visibilities per degridding work item: 8 warps x 4 visibilities.
