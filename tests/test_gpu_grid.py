@@ -244,3 +244,23 @@ def test_autotune_returns_a_valid_schedule(ctx):
     vd2, _keep2 = aw.device_observation(ob)
     info = aw.aw_plan_query(aw.aw_plan_create(ctx, vd2, kg))
     assert (info.tile, info.chunk) == (t.tile, t.chunk)
+
+
+def test_batched_graph_cache_alternates_between_argument_sets(ctx):
+    # the plan caches the graphs of the last two (vis, weight, grid, kset, stream) sets:
+    # alternating buffers, a third set evicting the least recently used, each result
+    # equal to the direct launch on the same inputs
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=8)
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, 0, 0))
+    vs = [torch.as_tensor(sy.random_vis(ob.nvis, 4, seed=s), device="cuda") for s in (1, 2, 3)]
+    ref = []
+    for v in vs:
+        g = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
+        aw.aw_grid(ctx, c.plan, c.kg, v, None, g)
+        ref.append(g.cpu().numpy())
+    for i in (0, 1, 0, 1, 2, 0, 2, 1):
+        g = torch.zeros((4, kw["N"], kw["N"]), dtype=torch.complex64, device="cuda")
+        aw.aw_grid_batched(ctx, c.plan, c.kg, vs[i], None, g)
+        l2, mx = rel_err(g.cpu().numpy(), ref[i])
+        assert l2 < 1e-6 and mx < 1e-6, (i, l2, mx)
