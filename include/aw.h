@@ -15,6 +15,9 @@
  *     default stream.  Work is enqueued asynchronously unless stated.
  *   - Opaque handles (aw_ctx, aw_kernel_set, aw_plan, aw_surrogate) are
  *     owned by the library and freed by the matching *_destroy call.
+ *   - Threads: a context and the handles used with it serve one host thread
+ *     at a time (the context caches cuFFT plans and scratch, a plan its
+ *     work queue and graphs); separate contexts may run concurrently.
  *
  * Conventions (shared by every call)
  *   - Grid of N x N uv cells (N a power of two, 16..16384), image cell dl
@@ -27,7 +30,9 @@
  *   - Degridding is V = sum I exp(-2 pi i (u l + v m + w (n - 1))) (Eq. 2 with
  *     the usual sign); gridding is its adjoint.
  *   - A visibility with w < 0 is handled at (-u, -v, -w) as P conj(V)
- *     (P swaps XY and YX), exact for baseline-averaged beams (Sec. 3.2).
+ *     (P swaps XY and YX): the reversed baseline, exact for baseline-averaged
+ *     beams (Sec. 3.2) and, with per-baseline kernels, taking the class of
+ *     the two antenna types in swapped order.
  */
 #ifndef AW_H
 #define AW_H
