@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
     ap.add_argument("--no-learned-degrid", action="store_true", help="skip the learned degridding comparison")
+    ap.add_argument("--learned-inline-case", type=int, default=None, metavar="ENGINE",
+                    help="only run the small inline-surrogate profiling case on engine 0 (mma.sync) or 1 (tcgen05)")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
     ap.add_argument("--no-mosaic", action="store_true", help="skip the mosaic measurements")
     ap.add_argument("--no-baselines", action="store_true", help="skip the per-baseline kernel measurement")
@@ -809,6 +811,47 @@ def learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, ch
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def learned_inline_case(engine: int):
+    """A small case for profiling the inline surrogate: the full-pol test geometry (256^2 x 4,
+    3 w planes x 2 PA x 2 frequency bins, supports 16-24, OS 8), 57,600 visibilities, a randomly
+    initialised 5 -> 128 x 4 -> 32 network; three untimed and one timed aw_grid_learned call."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import build as awbuild
+    from paper_2206_15117_gb300 import synthetic as sy
+    awbuild.build()
+    ctx = aw.aw_create(0)
+    ob = sy.small_observation(n_ant=16, radius_m=180.0, n_t=120, freq=(1.2e9, 1.3e9, 1.4e9, 1.5e9), npa=2, nfb=2,
+                              seed=sy.BASE_SEED + 300)
+    N = 256
+    kw = dict(N=N, dl=math.radians(3.0) / N, OS=8, W=7.0, npol=4, nw=3, w_max=ob.w_max, supports=[16, 20, 24],
+              pa=list(ob.pa_centres), fbin_freqs=list(ob.fbin_freqs), dish_d=12.0, d_xy=sy.LEAK_XY, d_yx=sy.LEAK_YX,
+              eps=0.2)
+    exact = aw.aw_make_kernels(ctx, **kw)
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, seed=5, D=1.0,
+                                 norm_supports=kw["supports"], w_max=kw["w_max"], f_c=1.35e9, f_h=0.15e9,
+                                 chi_c=0.0, chi_h=1.5, out_scale=0.02)
+    aw.aw_surrogate_set_engine(sur, engine)
+    vd, keep = aw.device_observation(ob)
+    plan = aw.aw_plan_create(ctx, vd, exact)
+    info = aw.aw_plan_query(plan)
+    vis = torch.as_tensor(sy.random_vis(ob.nvis, 4, seed=31), device="cuda")
+    grid = torch.zeros((4, N, N), dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        aw.aw_grid_learned(ctx, plan, sur, exact, vis, None, grid)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    aw.aw_grid_learned(ctx, plan, sur, exact, vis, None, grid)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    rows = info.mean_taps * info.nvalid
+    print(json.dumps({"case": "learned_inline", "engine": engine, "nvis": ob.nvis, "rows": rows, "ms": ms,
+                      "network_tflops": rows * 2 * (5 * 128 + 3 * 128 * 128 + 128 * 32) / (ms / 1e3) / 1e12}))
+    return 0
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2206_15117_gb300 import aw
@@ -1140,6 +1183,8 @@ def fp32_peak_tflops():
 
 def main():
     args = parse()
+    if args.learned_inline_case is not None:
+        return learned_inline_case(args.learned_inline_case)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
