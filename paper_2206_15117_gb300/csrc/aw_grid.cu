@@ -569,12 +569,15 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
         const int t0 = slab * DG_TS;
         const int ns = min(DG_TS, L - t0);
         const uint32_t dst = smem_u32(dsm) + (uint32_t)(b * TC::SLAB_BYTES);
-        for (int idx = threadIdx.x; idx < ns * TC::NCH; idx += blockDim.x) {
-            const int c = idx / ns, tl = idx - c * ns;
-            if (AW_BOK(kbase >= 0 && kbase + ((int64_t)c * L + t0 + tl + 1) * TC::CE <= a.tab_elems, BC_D_SRC) &&
-                AW_BOK(c < TC::NCH && tl < DG_TS, BC_D_DST))
-                cp_async_chunk<TC::CB>(dst + (uint32_t)((c * DG_TS + tl) * TC::CB),
-                                       src + ((int64_t)c * L + t0 + tl) * TC::CB);
+        // a thread per tap copies the tap's NCH chunks (one pass when blockDim.x == DG_TS);
+        // for each chunk index the lanes of a warp read consecutive 16-byte chunks
+        for (int tl = threadIdx.x; tl < ns; tl += blockDim.x) {
+            const char *s0 = src + ((int64_t)t0 + tl) * TC::CB;
+#pragma unroll
+            for (int c = 0; c < TC::NCH; ++c)
+                if (AW_BOK(kbase >= 0 && kbase + ((int64_t)c * L + t0 + tl + 1) * TC::CE <= a.tab_elems, BC_D_SRC) &&
+                    AW_BOK(tl < DG_TS, BC_D_DST))
+                    cp_async_chunk<TC::CB>(dst + (uint32_t)((c * DG_TS + tl) * TC::CB), s0 + (int64_t)c * L * TC::CB);
         }
         cp_async_commit();
     };
