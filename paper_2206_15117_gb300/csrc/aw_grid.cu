@@ -558,13 +558,25 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
     for (int s2 = 0; s2 < NPOL; ++s2) gplane[s2] = a.grid + (int64_t)s2 * a.N * a.N;
     const char *ktab = reinterpret_cast<const char *>(a.ktab);
 
-    // ---- staging of (item, slab) into buffer b
-    auto stage = [&](int64_t item, int slab, int b) {
+    // ---- an item's header: its records, support and kernel block
+    struct Hdr {
+        int start, count, S;
+        int64_t kbase;  // complex index of the kernel block in the table
+    };
+    auto load_hdr = [&](int64_t item) {
         const int4 it = a.items[item];
-        const int S = a.bin_support[it.z];
-        const int L = S * S;
+        Hdr h;
+        h.start = it.x;
+        h.count = it.y;
+        h.S = a.bin_support[it.z];
         const aw_rec r0 = a.rec_dg[it.x];
-        const int64_t kbase = a.bin_offset[it.z] + (int64_t)(r0.fy * a.OS + r0.fx) * L * P;  // complex index
+        h.kbase = a.bin_offset[it.z] + (int64_t)(r0.fy * a.OS + r0.fx) * h.S * h.S * P;
+        return h;
+    };
+    // ---- staging of slab `slab` of an item into buffer b
+    auto stage = [&](const Hdr &h, int slab, int b) {
+        const int L = h.S * h.S;
+        const int64_t kbase = h.kbase;
         const char *src = ktab + kbase * TC::EB;
         const int t0 = slab * DG_TS;
         const int ns = min(DG_TS, L - t0);
@@ -581,15 +593,17 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
         }
         cp_async_commit();
     };
-    auto nslabs = [&](int64_t item) {
-        const int S = a.bin_support[a.items[item].z];
-        return (S * S + DG_TS - 1) / DG_TS;
-    };
+    auto nslabs = [&](const Hdr &h) { return (h.S * h.S + DG_TS - 1) / DG_TS; };
 
     int64_t item = blockIdx.x;
     if (item < a.nitems) {
-        int slab = 0, nsl = nslabs(item), buf = 0;
-        stage(item, 0, 0);
+        // the next item's header is loaded as soon as an item starts, so that
+        // its latency hides behind the item's slabs
+        Hdr cur = load_hdr(item), nxt = cur;
+        bool nxt_ok = item + gridDim.x < a.nitems;
+        if (nxt_ok) nxt = load_hdr(item + gridDim.x);
+        int slab = 0, nsl = nslabs(cur), buf = 0;
+        stage(cur, 0, 0);
         // per-item state
         int start = 0, count = 0, S = 0, L = 0, ngp = 1, wpg = 8, g = 0, ph = 0;
         float invS = 1.f;
@@ -598,9 +612,8 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
         float acc[NV];
         for (;;) {
             if (slab == 0) {
-                const int4 it = a.items[item];
-                start = it.x; count = it.y;
-                S = a.bin_support[it.z];
+                start = cur.start; count = cur.count;
+                S = cur.S;
                 L = S * S;
                 invS = 1.0f / (float)S;
                 const int need = (count + VB - 1) / VB;
@@ -623,12 +636,10 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
                     if (AW_BOK(i < AW_DG_CHUNK * NPOL * 2, BC_D_OUT)) s_out[i] = 0.f;
             }
             // the next (item, slab) streams into the other buffer
-            int64_t nitem = item;
-            int nslab = slab + 1, nnsl = nsl;
-            if (nslab == nsl) { nitem = item + gridDim.x; nslab = 0; nnsl = nitem < a.nitems ? nslabs(nitem) : 0; }
-            const bool has_next = nitem < a.nitems;
+            const bool to_next = slab + 1 == nsl;
+            const bool has_next = !to_next || nxt_ok;
             if (has_next) {
-                stage(nitem, nslab, buf ^ 1);
+                stage(to_next ? nxt : cur, to_next ? 0 : slab + 1, buf ^ 1);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -722,9 +733,16 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
             }
             __syncthreads();  // buffer `buf` and s_out are free again
             if (!has_next) break;
-            item = nitem;
-            slab = nslab;
-            nsl = nnsl;
+            if (to_next) {
+                item += gridDim.x;
+                cur = nxt;
+                slab = 0;
+                nsl = nslabs(cur);
+                nxt_ok = item + gridDim.x < a.nitems;
+                if (nxt_ok) nxt = load_hdr(item + gridDim.x);
+            } else {
+                ++slab;
+            }
             buf ^= 1;
         }
     }
