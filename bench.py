@@ -989,8 +989,8 @@ def run_ours(args, rank, world, dist):
     # (the tile schedule depends on tile and chunk, the offset-grouped gridder on the super-tile and
     # the CTAs in flight, the degridder on the super-tile)
     measured_traffic = {("grid_persistent_kernel", 63851035, 64, 128): 149.65e9,
-                        ("grid_offset_kernel", 63851035, 1024, 5): 40.72e9,
-                        ("degrid_items_kernel", 63851035, 1024): 14.43e9}
+                        ("grid_offset_kernel", 63851035, 1024, 5): 44.46e9,
+                        ("degrid_items_kernel", 63851035, 1024): 13.96e9}
     kname = gname if g_ms >= d_ms else "degrid_items_kernel"
     if kname == "grid_persistent_kernel":
         dom_kernel = (kname, int(nvis), tune.tile, tune.chunk)

@@ -551,7 +551,12 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
     constexpr int NV = VB * NPOL * 2;  // partial sums per lane
     using TC = TabChunks<P, ST>;
     extern __shared__ __align__(16) char dsm[];
-    float *s_out = reinterpret_cast<float *>(dsm + 2 * TC::SLAB_BYTES);
+    // full-pol with 16-bit tables: each slab is widened to FP32 once, into s_f32, so
+    // that the eight warps reading every tap do not each convert it again
+    constexpr bool CONV = NPOL == 4 && ST != AW_STORAGE_FP32;
+    using TF = TabChunks<P, AW_STORAGE_FP32>;
+    char *s_f32 = dsm + 2 * TC::SLAB_BYTES;
+    float *s_out = reinterpret_cast<float *>(s_f32 + (CONV ? TF::SLAB_BYTES : 0));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float2 *gplane[NPOL];
 #pragma unroll
@@ -648,6 +653,22 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
             const char *sl = dsm + buf * TC::SLAB_BYTES;
             const int t0 = slab * DG_TS;
             const int ns = min(DG_TS, L - t0);
+            if constexpr (CONV) {
+                // row c of a tap: one 16-byte chunk of four 16-bit complex values in the
+                // staged slab, two chunks of two FP32 complex values in s_f32
+                for (int tl = threadIdx.x; tl < ns; tl += blockDim.x) {
+#pragma unroll
+                    for (int c = 0; c < NPOL; ++c) {
+                        float2 kr[NPOL];
+                        smem_krow<NPOL, ST>(sl, tl, c, kr);
+                        float4 *d = reinterpret_cast<float4 *>(s_f32);
+                        d[(2 * c) * DG_TS + tl] = make_float4(kr[0].x, kr[0].y, kr[1].x, kr[1].y);
+                        d[(2 * c + 1) * DG_TS + tl] = make_float4(kr[2].x, kr[2].y, kr[3].x, kr[3].y);
+                    }
+                }
+                __syncthreads();
+                sl = s_f32;
+            }
             for (int tl = ph * 32 + lane; tl < ns; tl += wpg * 32) {
                 const int t = t0 + tl;
                 const int jy = (int)(((float)t + 0.5f) * invS);
@@ -664,7 +685,7 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
 #pragma unroll
                 for (int c = 0; c < NPOL; ++c) {
                     float2 kr[NPOL];
-                    smem_krow<NPOL, ST>(sl, tl, c, kr);
+                    smem_krow<NPOL, CONV ? AW_STORAGE_FP32 : ST>(sl, tl, c, kr);
 #pragma unroll
                     for (int j = 0; j < VB; ++j) {
                         float re = acc[(j * NPOL + c) * 2], im = acc[(j * NPOL + c) * 2 + 1];
@@ -757,7 +778,10 @@ __global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
 
 template <int NPOL, int ST>
 size_t degrid_smem_bytes() {
-    return 2 * (size_t)TabChunks<NPOL * NPOL, ST>::SLAB_BYTES + sizeof(float) * AW_DG_CHUNK * NPOL * 2;
+    constexpr bool conv = NPOL == 4 && ST != AW_STORAGE_FP32;
+    return 2 * (size_t)TabChunks<NPOL * NPOL, ST>::SLAB_BYTES +
+           (conv ? (size_t)TabChunks<NPOL * NPOL, AW_STORAGE_FP32>::SLAB_BYTES : 0) +
+           sizeof(float) * AW_DG_CHUNK * NPOL * 2;
 }
 
 template <int NPOL, int ST>
