@@ -884,7 +884,7 @@ def run_ours(args, rank, world, dist):
     t0 = time.perf_counter()
     if args.tune:
         tv = [int(x) for x in args.tune.split(",")]
-        tune = aw.aw_tune(*(tv + [0] * (5 - len(tv))))
+        tune = aw.aw_tune(*(tv + [0] * (6 - len(tv))))
     else:
         tune = aw.aw_autotune(ctx, vd_sub, kg)
     t_tune = time.perf_counter() - t0
@@ -894,18 +894,32 @@ def run_ours(args, rank, world, dist):
     t_plan = time.perf_counter() - t0
     N = kw["N"]
     confirm = None
-    plan_alt, tune_alt = None, None  # the other gridding schedule, kept for the 16-bit variants
+    alt_plans = []  # the other schedules' plans, kept for the 16-bit variants
     if not args.tune:
-        # the subsample ranks the candidates; the two schedules are then timed once more on
-        # the full data (their DRAM behaviour differs with the number of bins in flight)
+        # the subsample ranks the candidates; the finalists are then timed once more on the
+        # full data (the schedules' DRAM behaviour, and how the two parts of the hybrid share
+        # the SMs, differ with the number of bins in flight): the tuned choice, the two plain
+        # schedules and the hybrid split where the low w planes hold about 25, 35 and 45 % of
+        # the visibility-taps, at 2 tile CTAs per SM
         t0 = time.perf_counter()
-        other = aw.aw_tune(tune.tile, tune.chunk, tune.ctas_per_sm, 1024,
-                           aw.AW_GRID_OFFSETS if tune.grid_mode == aw.AW_GRID_TILES else aw.AW_GRID_TILES)
-        plan2 = aw.aw_plan_create(ctx, vd, kg, tune=other)
+        cands = [(tune, plan)]
+        tiles_ctas = tune.ctas_per_sm if tune.grid_mode == aw.AW_GRID_TILES else 5
+        finalists = [aw.aw_tune(tune.tile, tune.chunk, tiles_ctas, 1024, aw.AW_GRID_TILES),
+                     aw.aw_tune(tune.tile, tune.chunk, tiles_ctas, 1024, aw.AW_GRID_OFFSETS)]
+        for share in (0.25, 0.35, 0.45):
+            finalists.append(aw.aw_tune(tune.tile, tune.chunk, 2, 1024, aw.AW_GRID_HYBRID,
+                                        hybrid_split(aw, plan, kw, share)))
+        key = lambda t_: (t_.grid_mode, t_.ctas_per_sm if t_.grid_mode != aw.AW_GRID_OFFSETS else 0,
+                          t_.split_planes if t_.grid_mode == aw.AW_GRID_HYBRID else 0, t_.dg_tile or 1024)
+        seen = {key(tune)}
+        for t_ in finalists:
+            if key(t_) not in seen:
+                seen.add(key(t_))
+                cands.append((t_, aw.aw_plan_create(ctx, vd, kg, tune=t_)))
         zv = torch.zeros((nvis, 4), dtype=torch.complex64, device=dev)
         gtmp = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
         times = []
-        for p_ in (plan, plan2):
+        for _, p_ in cands:
             ms = []
             for _ in range(3):
                 a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -915,14 +929,20 @@ def run_ours(args, rank, world, dist):
                 torch.cuda.synchronize()
                 ms.append(a_.elapsed_time(b_))
             times.append(min(ms[1:]))
-        names = [["tiles", "offsets"][t_.grid_mode] for t_ in (tune, other)]
-        confirm = {"full_data_grid_ms": dict(zip(names, times)), "seconds": None}
-        plan_alt, tune_alt = plan2, other
-        if times[1] < times[0]:
-            plan, tune, plan_alt, tune_alt = plan2, other, plan, tune
-        if args.no_variants:
-            plan_alt = tune_alt = None
-        del plan2, zv, gtmp
+        label = lambda t_: SCHEDULES[t_.grid_mode] + ("/%d/%d" % (t_.split_planes, t_.ctas_per_sm)
+                                                       if t_.grid_mode == aw.AW_GRID_HYBRID else "")
+        confirm = {"full_data_grid_ms": {label(t_): ms_ for (t_, _), ms_ in zip(cands, times)},
+                   "seconds": None}
+        best = int(np.argmin(times))
+        tune, plan = cands[best]
+        # the 16-bit variants choose between the best plan of each schedule
+        alt_plans = []
+        if not args.no_variants:
+            for mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS, aw.AW_GRID_HYBRID):
+                idx = [i for i, (t_, _) in enumerate(cands) if t_.grid_mode == mode and i != best]
+                if idx and mode != tune.grid_mode:
+                    alt_plans.append(cands[min(idx, key=lambda i: times[i])])
+        del cands, zv, gtmp
         torch.cuda.empty_cache()
         confirm["seconds"] = time.perf_counter() - t0
     info = aw.aw_plan_query(plan)
@@ -933,7 +953,9 @@ def run_ours(args, rank, world, dist):
     model = torch.randn((4, N, N), dtype=torch.complex64, device=dev, generator=gen)
     grid = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
     image = torch.empty((4, N, N), dtype=torch.float32, device=dev)
-    launches_per_step = 4   # grid (persistent), checker + grid-correction (FFT step), degrid
+    # grid (one kernel, or the two concurrent parts of the hybrid schedule), checker +
+    # grid-correction (FFT step), degrid
+    launches_per_step = 4 + (1 if tune.grid_mode == aw.AW_GRID_HYBRID else 0)
     # pinned host buffers of the end-to-end measurement, allocated up front: allocated after the
     # BF16/FP16 variant sets had been built and freed, the same transfers measured about 9x slower
     host_bufs = None
@@ -984,7 +1006,8 @@ def run_ours(args, rank, world, dist):
     flops = 128.0 * info.mean_taps * info.nvalid          # 16 complex MACs x 8 flop per tap
     g_ms, d_ms = statistics.mean(t_grid), statistics.mean(t_deg)
     dom_ms = max(g_ms, d_ms)
-    gname = "grid_offset_kernel" if tune.grid_mode == aw.AW_GRID_OFFSETS else "grid_persistent_kernel"
+    gname = {aw.AW_GRID_TILES: "grid_persistent_kernel", aw.AW_GRID_OFFSETS: "grid_offset_kernel",
+             aw.AW_GRID_HYBRID: "grid_persistent_kernel + grid_offset_kernel"}[tune.grid_mode]
     dom = ("aw_grid (%s)" % gname) if g_ms >= d_ms else "aw_degrid (degrid_items_kernel)"
     peak_tflops = fp32_peak_tflops()
     achieved = flops / (dom_ms / 1e3) / 1e12
@@ -994,9 +1017,15 @@ def run_ours(args, rank, world, dist):
     # the CTAs in flight, the degridder on the super-tile)
     measured_traffic = {("grid_persistent_kernel", 63851035, 64, 128): 149.65e9,
                         ("grid_offset_kernel", 63851035, 1024, 5): 44.46e9,
+                        ("hybrid", 63851035, 64, 128, 1024, 7, 2): 6.44e9 + 24.96e9,
                         ("degrid_items_kernel", 63851035, 1024): 13.96e9}
     kname = gname if g_ms >= d_ms else "degrid_items_kernel"
-    if kname == "grid_persistent_kernel":
+    if tune.grid_mode == aw.AW_GRID_HYBRID and g_ms >= d_ms:
+        # the two parts of one gridding step (tile kernel on the low w planes, offset kernel on
+        # the rest): their DRAM bytes added
+        dom_kernel = ("hybrid", int(nvis), tune.tile, tune.chunk, tune.dg_tile or 1024, tune.split_planes,
+                      tune.ctas_per_sm)
+    elif kname == "grid_persistent_kernel":
         dom_kernel = (kname, int(nvis), tune.tile, tune.chunk)
     elif kname == "grid_offset_kernel":
         dom_kernel = (kname, int(nvis), tune.dg_tile or 1024, tune.ctas_per_sm)
@@ -1012,7 +1041,7 @@ def run_ours(args, rank, world, dist):
     # variants: BF16 / FP16 kernel tables (FP32 arithmetic).  Without --tune each precision grids
     # with the faster of the two schedules on its own tables, as aw_autotune on that kernel set would
     # choose (halving the table bytes moves the tile schedule's L2 stream, not the atomics)
-    schedules = ["tiles", "offsets"]
+    schedules = SCHEDULES
     variants = {"fp32": {"grid_ms": g_ms, "degrid_ms": d_ms, "mvis_s": nvis / ((g_ms + d_ms) / 1e3) / 1e6,
                          "grid_schedule": schedules[tune.grid_mode]}}
     if not args.no_variants:
@@ -1020,9 +1049,7 @@ def run_ours(args, rank, world, dist):
             kg2 = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID, storage=stg)
             kd2 = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID, storage=stg)
             res = {}
-            for pl, tn in ((plan, tune), (plan_alt, tune_alt)):
-                if pl is None:
-                    continue
+            for tn, pl in [(tune, plan)] + alt_plans:
                 step(None, kg2, kd2, pl)
                 ev2 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(3)]
                 for k in range(3):
@@ -1037,7 +1064,7 @@ def run_ours(args, rank, world, dist):
                               "table_bytes": int(aw.aw_kernel_set_info(kg2).bytes)}
             del kg2, kd2
             torch.cuda.empty_cache()
-    plan_alt = None
+    alt_plans = []
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -1169,7 +1196,8 @@ def run_ours(args, rank, world, dist):
                 "gpu_launches": launches_per_step * args.steps,
                 "tune": {"tile": tune.tile, "chunk": tune.chunk, "ctas_per_sm": tune.ctas_per_sm,
                          "dg_tile": tune.dg_tile or 1024, "degrid_items": info.nitems_degrid,
-                         "grid_schedule": ["tiles", "offsets"][tune.grid_mode], "confirmed": confirm},
+                         "grid_schedule": SCHEDULES[tune.grid_mode], "split_planes": tune.split_planes,
+                         "confirmed": confirm},
                 "clean": clean, "mosaic": mosaic, "per_baseline_kernels": baselines, "learned": learned}
         print(json.dumps(line), flush=True)
     return 0
@@ -1186,6 +1214,27 @@ def aggregate(total_ms: float, nvis: int, dist=None, device=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(n, op=dist.ReduceOp.SUM)
     return float(t.item()), int(n.item())
+
+
+SCHEDULES = ["tiles", "offsets", "hybrid"]
+
+
+def hybrid_split(aw, plan, kw, share: float) -> int:
+    """Number of low w planes that hold about `share` of the plan's
+    visibility-taps (sum of S^2), from the plan's own bins; 1..nw-1."""
+    import torch
+    info = aw.aw_plan_query(plan)
+    b = torch.empty(int(info.nvis), dtype=torch.int32, device="cuda")
+    v = torch.empty(int(info.nvis), dtype=torch.uint8, device="cuda")
+    aw.aw_plan_coords(plan, bin=b, valid=v)
+    per_plane = len(kw["pa"]) * len(kw["fbin_freqs"])
+    bins = b[v == 1].to(torch.int64)
+    planes = (bins // per_plane) % kw["nw"]
+    sup = torch.as_tensor(kw["supports"], dtype=torch.float64, device=bins.device)
+    taps = torch.bincount(planes, weights=sup[planes] ** 2, minlength=kw["nw"]).cpu().numpy()
+    cum = np.cumsum(taps) / max(taps.sum(), 1.0)       # cum[q - 1]: share of planes < q
+    q = int(np.searchsorted(cum, share)) + 1
+    return max(1, min(q, kw["nw"] - 1))
 
 
 def fp32_peak_tflops():

@@ -150,7 +150,10 @@ typedef struct aw_tune {
     int32_t dg_tile;         /* degridding super-tile side (power of 2, 32..4096);
                               * 0 selects 1024.  Degridding visits visibilities
                               * grouped by (bin, super-tile, oversampled offset) */
-    int32_t grid_mode;       /* AW_GRID_TILES or AW_GRID_OFFSETS (below)           */
+    int32_t grid_mode;       /* AW_GRID_TILES, AW_GRID_OFFSETS or AW_GRID_HYBRID  */
+    int32_t split_planes;    /* AW_GRID_HYBRID: visibilities in w planes
+                              * [0, split_planes) take the TILES schedule, the
+                              * rest OFFSETS; 0..nw.  Ignored by the other modes */
 } aw_tune;
 
 /* Gridding schedules (aw_tune.grid_mode).  TILES: work items of one bin and
@@ -158,9 +161,15 @@ typedef struct aw_tune {
  * persistent launch (tile, chunk, ctas_per_sm apply).  OFFSETS: the
  * degridding items (one bin, super-tile and oversampled offset), each kernel
  * tap loaded once per item and added for every visibility with vector
- * atomics (dg_tile applies).  Both give the same grid up to FP32 rounding
- * order. */
-enum { AW_GRID_TILES = 0, AW_GRID_OFFSETS = 1 };
+ * atomics (dg_tile applies).  HYBRID: the low w planes (the small supports,
+ * split_planes of them) on TILES and the others on OFFSETS, the two kernels
+ * running at the same time on two streams (the plan owns the second stream;
+ * the call forks from and joins back into the caller's stream, also inside
+ * the graph of aw_grid_batched).  The TILES kernel is bound by the L2->SM
+ * stream of kernel values, the OFFSETS kernel by its atomics, so sharing the
+ * SMs between them beats either alone.  All modes give the same grid up to
+ * FP32 rounding order. */
+enum { AW_GRID_TILES = 0, AW_GRID_OFFSETS = 1, AW_GRID_HYBRID = 2 };
 
 typedef struct aw_plan_info {
     int64_t nvis;
@@ -272,7 +281,9 @@ int aw_kernel_set_destroy(aw_kernel_set *kset);
  * The plan depends on the kernel set only through N, OS, the bins and their
  * supports; any set with the same geometry may be used with it.
  * tune == NULL uses the last aw_autotune result of this context (its cache),
- * or tile 32, chunk 256 if the context has none.  Synchronises `stream`.
+ * or tile 32, chunk 256 if the context has none; a cached HYBRID tune whose
+ * split_planes is not inside 1..nw-1 of this kernel set is used with the
+ * OFFSETS schedule instead.  Synchronises `stream`.
  */
 int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset,
                    const aw_tune *tune, aw_plan **out, void *stream);
@@ -338,9 +349,11 @@ int aw_grid_batched(aw_ctx *ctx, aw_plan *plan, const aw_kernel_set *kset, const
 
 /*
  * aw_autotune - time aw_grid_batched over candidate (tile, chunk,
- * ctas_per_sm) of the TILES schedule and two super-tile sizes of the OFFSETS
- * schedule on the given visibilities (pass a subsample to keep it short) and
- * return the fastest in *out; it is also kept in the context as the tune
+ * ctas_per_sm) of the TILES schedule, two super-tile sizes of the OFFSETS
+ * schedule and up to three split planes (the first planes holding about 25,
+ * 35 and 45 % of the visibility-taps) at 2 or 3 TILES CTAs per SM of the
+ * HYBRID schedule on the given visibilities (pass a subsample to keep it
+ * short) and return the fastest in *out; it is also kept in the context as the tune
  * aw_plan_create uses when given NULL.  Uses a scratch grid it allocates.
  * Synchronises `stream`.
  */

@@ -231,6 +231,11 @@ static void free_plan(aw_plan *p) {
     if (p->d_wsum) aw_dev_free(p->d_wsum);
     if (p->d_nonfinite) aw_dev_free(p->d_nonfinite);
     if (p->d_counter) aw_dev_free(p->d_counter);
+    if (p->d_items_ht) aw_dev_free(p->d_items_ht);
+    if (p->d_items_ho) aw_dev_free(p->d_items_ho);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->aux) cudaStreamDestroy(p->aux);
     delete p;
 }
 
@@ -243,7 +248,15 @@ int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kse
     if (rc) return rc;
     aw_plan *p = new aw_plan();
     p->device = ctx->device;
-    if (!tune && ctx->has_tune) tune = &ctx->tune_cache;
+    aw_tune cached{};
+    if (!tune && ctx->has_tune) {
+        // a cached hybrid split names planes of the set it was tuned on: a set
+        // without planes on both sides of it takes the offset schedule instead
+        cached = ctx->tune_cache;
+        if (cached.grid_mode == AW_GRID_HYBRID && (cached.split_planes < 1 || cached.split_planes >= kset->spec.nw))
+            cached.grid_mode = AW_GRID_OFFSETS;
+        tune = &cached;
+    }
     rc = aw_plan_build(ctx, vis, kset, tune, p, S_(stream));
     if (rc != AW_OK) { free_plan(p); return rc; }
     *out = p;
@@ -315,6 +328,38 @@ static int fill_stats(const aw_plan *p, aw_stats *stats, cudaStream_t s) {
     return AW_OK;
 }
 
+// The plan's gridding schedule on stream s.  AW_GRID_HYBRID forks: the TILES
+// part (persistent, its d_counter zeroed by the caller) runs on s, the OFFSETS
+// part on the plan's second stream, sized to fit beside the TILES CTAs, and s
+// then waits for both; inside a stream capture the fork and join become edges
+// of the graph.
+static int launch_planned(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k, const void *vis,
+                          const float *weight, void *grid, bool persistent, cudaStream_t s) {
+    auto ctas_for = [&](int64_t n) {
+        const int64_t c = std::min<int64_t>((int64_t)ctx->sm_count * p->tune.ctas_per_sm, n);
+        return (int)std::max<int64_t>(c, 1);
+    };
+    if (p->tune.grid_mode != AW_GRID_HYBRID) {
+        aw_grid_launch L{p, k, vis, weight, grid, persistent, ctas_for(p->nitems), s};
+        return aw_launch_grid(L);
+    }
+    if (p->nitems == 0) return AW_OK;
+    if (!p->aux) return aw_set_error(AW_EINVAL, "hybrid plan without its second stream");
+    AW_CUDA_TRY(cudaEventRecord(p->ev_fork, s));
+    AW_CUDA_TRY(cudaStreamWaitEvent(p->aux, p->ev_fork, 0));
+    aw_grid_launch Lt{p, k, vis, weight, grid, true, ctas_for(p->nitems_ht), s,
+                      AW_GRID_TILES, p->d_items_ht, p->nitems_ht};
+    int rc = aw_launch_grid(Lt);
+    if (rc == AW_OK) {
+        aw_grid_launch Lo{p, k, vis, weight, grid, false, 0, p->aux, AW_GRID_OFFSETS, p->d_items_ho, p->nitems_ho};
+        rc = aw_launch_grid(Lo);
+    }
+    // joined even after a failed launch, so that a capture is not left forked
+    AW_CUDA_TRY(cudaEventRecord(p->ev_join, p->aux));
+    AW_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_join, 0));
+    return rc;
+}
+
 int aw_grid(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k, const void *vis, const float *weight,
             void *grid, aw_stats *stats, void *stream) {
     AW_GUARD_BEGIN
@@ -327,8 +372,8 @@ int aw_grid(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k, const void *v
     cudaStream_t s = S_(stream);
     AW_CUDA_TRY(cudaMemsetAsync(p->d_wsum, 0, sizeof(double), s));
     AW_CUDA_TRY(cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), s));
-    aw_grid_launch L{p, k, vis, weight, grid, false, 0, s};
-    rc = aw_launch_grid(L);
+    if (p->tune.grid_mode == AW_GRID_HYBRID) AW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), s));
+    rc = launch_planned(ctx, p, k, vis, weight, grid, false, s);
     if (rc) return rc;
     if (stats) return fill_stats(p, stats, s);
     return AW_OK;
@@ -373,15 +418,12 @@ int aw_grid_batched(aw_ctx *ctx, aw_plan *p, const aw_kernel_set *k, const void 
         cudaStream_t cap;
         AW_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
-        int ctas = ctx->sm_count * p->tune.ctas_per_sm;
-        if (ctas > p->nitems) ctas = (int)p->nitems;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
             cudaMemsetAsync(p->d_wsum, 0, sizeof(double), cap);
             cudaMemsetAsync(p->d_nonfinite, 0, sizeof(unsigned long long), cap);
             cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned int), cap);
-            aw_grid_launch L{p, k, vis, weight, grid, true, ctas, cap};
-            rc = aw_launch_grid(L);
+            rc = launch_planned(ctx, p, k, vis, weight, grid, true, cap);
             e = cudaStreamEndCapture(cap, &g);
         }
         if (e == cudaSuccess && rc == AW_OK) e = cudaGraphInstantiate(&slot->exec, g, 0);
@@ -473,6 +515,39 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
         free_plan(p);
         if (rc) break;
         if (ms_best < best) { best = ms_best; bt = tu; }
+    }
+    // the hybrid schedule: the first planes holding about a quarter to a half
+    // of the visibility-taps on TILES, the rest on OFFSETS, at 2 or 3 TILES CTAs per SM
+    std::vector<double> cum;
+    if (!rc) {
+        aw_tune tu{bt.tile, bt.chunk, 2, bt.dg_tile ? bt.dg_tile : 1024, AW_GRID_TILES};
+        aw_plan *p = new aw_plan();
+        p->device = ctx->device;
+        rc = aw_plan_build(ctx, vis, k, &tu, p, s);
+        if (!rc) rc = aw_plan_plane_taps(p, cum, s);
+        free_plan(p);
+    }
+    int last_q = -1;
+    const double targets[] = {0.25, 0.35, 0.45};
+    for (double target : targets) {
+        if (rc || cum.empty()) break;
+        int q = 1;
+        while (q < (int)cum.size() - 1 && cum[q] < target) ++q;   // cum[q]: share of planes < q
+        if (q <= last_q || q >= (int)cum.size() - 1) continue;
+        last_q = q;
+        aw_tune tu{bt.tile, bt.chunk, 2, bt.dg_tile ? bt.dg_tile : 1024, AW_GRID_HYBRID, q};
+        aw_plan *p = new aw_plan();
+        p->device = ctx->device;
+        rc = aw_plan_build(ctx, vis, k, &tu, p, s);
+        if (rc) { free_plan(p); break; }
+        for (int cp : {2, 3}) {
+            p->tune.ctas_per_sm = cp;
+            float ms_best = 1e30f;
+            rc = time_plan(p, &ms_best);
+            if (rc) break;
+            if (ms_best < best) { best = ms_best; bt = p->tune; }
+        }
+        free_plan(p);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

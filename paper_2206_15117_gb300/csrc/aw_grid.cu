@@ -820,12 +820,37 @@ int launch_degrid_t(const DegridArgs &a, int sm_count, cudaStream_t s) {
 }
 
 
+// CTAs per SM of the offset kernel that fit beside `tiles_per_sm` resident
+// CTAs of the persistent tile kernel (registers, shared memory, threads), so
+// that the two parts of the hybrid schedule run together in any launch order.
 template <int NPOL, int ST>
-int launch_grid_offset_t(const GridOffArgs &a, int sm_count, cudaStream_t s) {
+int offsets_beside_tiles(int tiles_per_sm, int chunk, int alone) {
+    cudaFuncAttributes ft{}, fo{};
+    if (cudaFuncGetAttributes(&ft, grid_persistent_kernel<NPOL, ST>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fo, grid_offset_kernel<NPOL, ST>) != cudaSuccess)
+        return 1;
+    int dev = 0, regs_sm = 65536, smem_sm = 233472, thr_sm = 2048;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    auto regs_cta = [](int r) { return ((r + 7) / 8) * 8 * 256; };  // 256 threads, 8-register steps
+    const int reserve = 1024;                                       // per-CTA shared memory the system keeps
+    const int smem_t = (int)SmemLayout<NPOL>::bytes(chunk) + (int)ft.sharedSizeBytes + reserve;
+    const int smem_o = (int)fo.sharedSizeBytes + reserve;
+    int n = (regs_sm - tiles_per_sm * regs_cta(ft.numRegs)) / regs_cta(fo.numRegs);
+    n = std::min(n, (smem_sm - tiles_per_sm * smem_t) / smem_o);
+    n = std::min(n, (thr_sm - tiles_per_sm * 256) / 256);
+    return std::max(1, std::min(n, alone));
+}
+
+template <int NPOL, int ST>
+int launch_grid_offset_t(const GridOffArgs &a, int sm_count, cudaStream_t s, int beside_tiles = 0, int chunk = 0) {
     // one wave of resident CTAs striding over the items in order, so that the
     // items in flight share bins and super-tiles (L2 locality)
     int per_sm = 1;
     AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_offset_kernel<NPOL, ST>, 256, 0));
+    if (beside_tiles > 0) per_sm = offsets_beside_tiles<NPOL, ST>(beside_tiles, chunk, std::max(per_sm, 1));
     int64_t blocks = a.nitems;
     const int64_t cap = (int64_t)sm_count * std::max(per_sm, 1);
     if (blocks > cap) blocks = cap;
@@ -840,8 +865,9 @@ int launch_grid_offsets(const aw_grid_launch &L) {
     const aw_kernel_set *k = L.kset;
     GridOffArgs a;
     a.rec_dg = p->d_rec_dg;
-    a.items = p->d_items_dg;
-    a.nitems = p->nitems_dg;
+    a.items = L.mode >= 0 ? L.items : p->d_items_dg;
+    a.nitems = L.mode >= 0 ? L.nitems : p->nitems_dg;
+    if (a.nitems == 0) return AW_OK;
     a.ktab = k->d_table;
     a.bin_offset = k->d_bin_offset;
     a.bin_support = k->d_bin_support;
@@ -860,14 +886,16 @@ int launch_grid_offsets(const aw_grid_launch &L) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int st = k->spec.storage;
+    // as a part of the hybrid schedule: leave room for the tile kernel's CTAs
+    const int bt = L.mode >= 0 ? p->tune.ctas_per_sm : 0, ch = p->tune.chunk;
     if (p->npol == 1) {
-        if (st == AW_STORAGE_FP32) return launch_grid_offset_t<1, AW_STORAGE_FP32>(a, sms, L.stream);
-        if (st == AW_STORAGE_BF16) return launch_grid_offset_t<1, AW_STORAGE_BF16>(a, sms, L.stream);
-        return launch_grid_offset_t<1, AW_STORAGE_FP16>(a, sms, L.stream);
+        if (st == AW_STORAGE_FP32) return launch_grid_offset_t<1, AW_STORAGE_FP32>(a, sms, L.stream, bt, ch);
+        if (st == AW_STORAGE_BF16) return launch_grid_offset_t<1, AW_STORAGE_BF16>(a, sms, L.stream, bt, ch);
+        return launch_grid_offset_t<1, AW_STORAGE_FP16>(a, sms, L.stream, bt, ch);
     }
-    if (st == AW_STORAGE_FP32) return launch_grid_offset_t<4, AW_STORAGE_FP32>(a, sms, L.stream);
-    if (st == AW_STORAGE_BF16) return launch_grid_offset_t<4, AW_STORAGE_BF16>(a, sms, L.stream);
-    return launch_grid_offset_t<4, AW_STORAGE_FP16>(a, sms, L.stream);
+    if (st == AW_STORAGE_FP32) return launch_grid_offset_t<4, AW_STORAGE_FP32>(a, sms, L.stream, bt, ch);
+    if (st == AW_STORAGE_BF16) return launch_grid_offset_t<4, AW_STORAGE_BF16>(a, sms, L.stream, bt, ch);
+    return launch_grid_offset_t<4, AW_STORAGE_FP16>(a, sms, L.stream, bt, ch);
 }
 
 }  // namespace
@@ -876,11 +904,14 @@ int aw_launch_grid(const aw_grid_launch &L) {
     const aw_plan *p = L.plan;
     const aw_kernel_set *k = L.kset;
     if (p->nitems == 0) return AW_OK;
-    if (p->tune.grid_mode == AW_GRID_OFFSETS) return launch_grid_offsets(L);
+    const int mode = L.mode >= 0 ? L.mode : p->tune.grid_mode;
+    if (mode == AW_GRID_HYBRID) return aw_set_error(AW_EINVAL, "hybrid schedule launched as one part");
+    if (mode == AW_GRID_OFFSETS) return launch_grid_offsets(L);
     GridArgs a;
     a.rec = p->d_rec;
-    a.items = p->d_items;
-    a.nitems = p->nitems;
+    a.items = L.mode >= 0 ? L.items : p->d_items;
+    a.nitems = L.mode >= 0 ? L.nitems : p->nitems;
+    if (a.nitems == 0) return AW_OK;
     a.ktab = k->d_table;
     a.bin_offset = k->d_bin_offset;
     a.bin_support = k->d_bin_support;

@@ -136,6 +136,15 @@ struct aw_plan {
     double *d_wsum = nullptr;
     unsigned long long *d_nonfinite = nullptr;
     unsigned int *d_counter = nullptr;  // persistent work-queue head
+    // AW_GRID_HYBRID: the gridding items of the low w planes (TILES) and the
+    // degridding items of the others (OFFSETS), and the second stream the
+    // OFFSETS part runs on (fork and join through the two events)
+    int4 *d_items_ht = nullptr;
+    int64_t nitems_ht = 0;
+    int4 *d_items_ho = nullptr;
+    int64_t nitems_ho = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // coordinate inputs kept for aw_plan_coords
     aw_vis_desc vis{};
     double uscale = 0, half = 0, winv = 0;
@@ -198,8 +207,15 @@ struct aw_grid_launch {
     bool persistent;
     int ctas;
     cudaStream_t stream;
+    // one schedule over a subset of its items (the parts of AW_GRID_HYBRID);
+    // mode < 0: the plan's own schedule over all its items
+    int mode = -1;
+    const int4 *items = nullptr;
+    int64_t nitems = 0;
 };
 int aw_launch_grid(const aw_grid_launch &L);
+// cum[q] = share of the plan's visibility-taps (sum of S^2) in w planes < q, q = 0..nw
+int aw_plan_plane_taps(const aw_plan *plan, std::vector<double> &cum, cudaStream_t s);
 int aw_launch_degrid(const aw_plan *plan, const aw_kernel_set *kset, const void *grid,
                      void *vis_out, cudaStream_t stream, const void *sub_from = nullptr);
 int aw_fft_to_image_impl(aw_ctx *ctx, int N, int npol, double W, void *grid, double weight_sum,

@@ -412,6 +412,54 @@ int build_items(const uint64_t *keys, int64_t nv, int shift, int chunk, const aw
 
 }  // namespace
 
+// AW_GRID_HYBRID: the gridding items of w planes [0, split_planes) for the
+// TILES part and the degridding items of the other planes for the OFFSETS
+// part (order kept), plus the second stream and the fork / join events.  The
+// w plane of bin ((k nw + p) npa + a) nfb + f is p.  Once per plan, on the host.
+static int build_hybrid_items(aw_plan *plan, cudaStream_t s) {
+    const int split = plan->tune.split_planes, per_plane = plan->npa * plan->nfb;
+    auto filter = [&](const int4 *d_src, int64_t n, bool low, int4 **d_out, int64_t *n_out) -> int {
+        std::vector<int4> h((size_t)n), keep;
+        if (n) AW_CUDA_TRY(cudaMemcpyAsync(h.data(), d_src, sizeof(int4) * n, cudaMemcpyDeviceToHost, s));
+        AW_CUDA_TRY(cudaStreamSynchronize(s));
+        keep.reserve((size_t)n);
+        for (const int4 &it : h)
+            if (((it.z / per_plane) % plan->nw < split) == low) keep.push_back(it);
+        *n_out = (int64_t)keep.size();
+        if (!keep.empty()) {
+            AW_CUDA_TRY(aw_dev_malloc(d_out, sizeof(int4) * keep.size()));
+            AW_CUDA_TRY(cudaMemcpyAsync(*d_out, keep.data(), sizeof(int4) * keep.size(), cudaMemcpyHostToDevice, s));
+            AW_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        return AW_OK;
+    };
+    int rc = filter(plan->d_items, plan->nitems, true, &plan->d_items_ht, &plan->nitems_ht);
+    if (rc) return rc;
+    rc = filter(plan->d_items_dg, plan->nitems_dg, false, &plan->d_items_ho, &plan->nitems_ho);
+    if (rc) return rc;
+    AW_CUDA_TRY(cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking));
+    AW_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming));
+    AW_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming));
+    return AW_OK;
+}
+
+int aw_plan_plane_taps(const aw_plan *plan, std::vector<double> &cum, cudaStream_t s) {
+    cum.assign((size_t)plan->nw + 1, 0.0);
+    std::vector<int4> h((size_t)plan->nitems);
+    if (plan->nitems) AW_CUDA_TRY(cudaMemcpyAsync(h.data(), plan->d_items, sizeof(int4) * plan->nitems,
+                                                  cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    const int per_plane = plan->npa * plan->nfb;
+    for (const int4 &it : h) {
+        const double S = plan->bin_support[(size_t)it.z];
+        cum[(size_t)((it.z / per_plane) % plan->nw) + 1] += (double)it.y * S * S;
+    }
+    for (size_t q = 1; q < cum.size(); ++q) cum[q] += cum[q - 1];
+    if (cum.back() > 0)
+        for (double &c : cum) c /= cum.back();
+    return AW_OK;
+}
+
 int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, const aw_tune *tune,
                   aw_plan *plan, cudaStream_t s) {
     (void)ctx;
@@ -426,8 +474,10 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     if (t.dg_tile == 0) t.dg_tile = 1024;
     if (t.dg_tile < 32 || t.dg_tile > 4096 || (t.dg_tile & (t.dg_tile - 1)))
         return aw_set_error(AW_EINVAL, "dg_tile %d", t.dg_tile);
-    if (t.grid_mode != AW_GRID_TILES && t.grid_mode != AW_GRID_OFFSETS)
+    if (t.grid_mode != AW_GRID_TILES && t.grid_mode != AW_GRID_OFFSETS && t.grid_mode != AW_GRID_HYBRID)
         return aw_set_error(AW_EINVAL, "grid_mode %d", t.grid_mode);
+    if (t.grid_mode == AW_GRID_HYBRID && (t.split_planes < 0 || t.split_planes > sp.nw))
+        return aw_set_error(AW_EINVAL, "split_planes %d outside 0..%d", t.split_planes, sp.nw);
     plan->tune = t;
     plan->dg_tile = t.dg_tile;
     plan->nvis = vis->nvis;
@@ -527,6 +577,10 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     rc = build_items(k0, nv, 2 * stbits, AW_DG_CHUNK, plan->d_rec_dg, counts, offs, bscratch.p,
                      &plan->d_items_dg, &plan->nitems_dg, s);
     if (rc) return rc;
+    if (t.grid_mode == AW_GRID_HYBRID) {
+        rc = build_hybrid_items(plan, s);
+        if (rc) return rc;
+    }
     AW_CUDA_TRY(cudaStreamSynchronize(s));
     return AW_OK;
 }

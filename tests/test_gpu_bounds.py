@@ -1,6 +1,6 @@
 """The bounds-checked build of the library (-DAW_BOUNDS_CHECK: the gridding
 and degridding kernels check every grid, table, shared-memory, record and
-output index and record the first bad one) run over both gridding schedules,
+output index and record the first bad one) run over the three gridding schedules,
 several tile / chunk / super-tile choices, ragged and flagged inputs, the
 subtracting degridder, full-pol and Stokes-I cases: no check may fail, and the
 results still match the FP64 oracle.  The library is built and loaded in a
@@ -31,8 +31,9 @@ SCRIPT = textwrap.dedent('''
     ctx = aw.aw_create(0)
     report = {}
     cases = [("fullpol", case_fullpol(n_t=12), [(8, 32, 3, 0, 0), (64, 128, 4, 256, 1), (32, 256, 2, 1024, 1),
-                                                 (16, 512, 2, 32, 0)]),
-             ("stokes_i", case_stokes_i_cfg1(time_samples=20), [(16, 128, 2, 0, 0), (32, 256, 2, 256, 1)])]
+                                                 (16, 512, 2, 32, 0), (32, 256, 2, 256, 2, 1)]),
+             ("stokes_i", case_stokes_i_cfg1(time_samples=20), [(16, 128, 2, 0, 0), (32, 256, 2, 256, 1),
+                                                              (16, 128, 3, 256, 2, 1)])]
     for name, (ob, kw), tunes in cases:
         npol, N = kw["npol"], kw["N"]
         kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)

@@ -230,13 +230,44 @@ def test_offset_schedule_grid(ctx, which, dg_tile):
     _check_grid(c, batched=True)
 
 
+# The hybrid schedule (the first split_planes w planes on TILES, the rest on
+# OFFSETS, the two kernels on two streams) against the same oracle: every
+# split from all-OFFSETS to all-TILES, direct and graph-captured, with the
+# statistics of both parts added together.
+@pytest.mark.parametrize("which,split", [("wproj", 0), ("wproj", 8), ("wproj", 32), ("fullpol", 1), ("fullpol", 2),
+                                         ("fullpol", 3)])
+def test_hybrid_schedule_grid(ctx, which, split):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = {"wproj": lambda: case_wproj(vis_fraction=0.002), "fullpol": case_fullpol}[which]()
+    split = min(split, kw["nw"])
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_HYBRID, split))
+    assert aw.aw_plan_query(c.plan).nitems > 0
+    _check_grid(c)
+    _check_grid(c, batched=True)
+    _check_grid(c, batched=True)  # the cached graph again
+    _check_degrid(c)
+
+
+def test_hybrid_split_must_name_planes(ctx):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(n_t=6)
+    kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
+    vd, _keep = aw.device_observation(ob)
+    for bad in (-1, kw["nw"] + 1):
+        with pytest.raises(aw.AWError) as ei:
+            aw.aw_plan_create(ctx, vd, kg, tune=aw.aw_tune(32, 256, 2, 0, aw.AW_GRID_HYBRID, bad))
+        assert ei.value.code == aw.AW_EINVAL
+
+
 def test_autotune_returns_a_valid_schedule(ctx):
     from paper_2206_15117_gb300 import aw
     ob, kw = case_fullpol(n_t=12)
     kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
     vd, _keep = aw.device_observation(ob)
     t = aw.aw_autotune(ctx, vd, kg)
-    assert t.grid_mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS)
+    assert t.grid_mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS, aw.AW_GRID_HYBRID)
+    if t.grid_mode == aw.AW_GRID_HYBRID:
+        assert 0 < t.split_planes < kw["nw"] and t.ctas_per_sm in (2, 3)
     assert t.tile in (16, 32, 64) and t.chunk in (128, 256, 512)
     if t.grid_mode == aw.AW_GRID_OFFSETS:
         assert t.dg_tile in (256, 1024)
