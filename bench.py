@@ -899,14 +899,14 @@ def run_ours(args, rank, world, dist):
         # the subsample ranks the candidates; the finalists are then timed once more on the
         # full data (the schedules' DRAM behaviour, and how the two parts of the hybrid share
         # the SMs, differ with the number of bins in flight): the tuned choice, the two plain
-        # schedules and the hybrid split where the low w planes hold about 25, 35 and 45 % of
-        # the visibility-taps, at 2 tile CTAs per SM
+        # schedules and the hybrid split where the low w planes hold nearest to 25, 30, 35 and
+        # 40 % of the visibility-taps, at 2 tile CTAs per SM
         t0 = time.perf_counter()
         cands = [(tune, plan)]
         tiles_ctas = tune.ctas_per_sm if tune.grid_mode == aw.AW_GRID_TILES else 5
         finalists = [aw.aw_tune(tune.tile, tune.chunk, tiles_ctas, 1024, aw.AW_GRID_TILES),
                      aw.aw_tune(tune.tile, tune.chunk, tiles_ctas, 1024, aw.AW_GRID_OFFSETS)]
-        for share in (0.25, 0.35, 0.45):
+        for share in (0.25, 0.30, 0.35, 0.40):
             finalists.append(aw.aw_tune(tune.tile, tune.chunk, 2, 1024, aw.AW_GRID_HYBRID,
                                         hybrid_split(aw, plan, kw, share)))
         key = lambda t_: (t_.grid_mode, t_.ctas_per_sm if t_.grid_mode != aw.AW_GRID_OFFSETS else 0,
@@ -1017,7 +1017,9 @@ def run_ours(args, rank, world, dist):
     # the CTAs in flight, the degridder on the super-tile)
     measured_traffic = {("grid_persistent_kernel", 63851035, 64, 128): 149.65e9,
                         ("grid_offset_kernel", 63851035, 1024, 5): 44.46e9,
+                        ("hybrid", 63851035, 64, 128, 1024, 6, 2): 5.60e9 + 26.88e9,
                         ("hybrid", 63851035, 64, 128, 1024, 7, 2): 6.44e9 + 24.96e9,
+                        ("hybrid", 63851035, 64, 128, 1024, 8, 2): 7.20e9 + 24.75e9,
                         ("degrid_items_kernel", 63851035, 1024): 13.96e9}
     kname = gname if g_ms >= d_ms else "degrid_items_kernel"
     if tune.grid_mode == aw.AW_GRID_HYBRID and g_ms >= d_ms:
@@ -1220,8 +1222,8 @@ SCHEDULES = ["tiles", "offsets", "hybrid"]
 
 
 def hybrid_split(aw, plan, kw, share: float) -> int:
-    """Number of low w planes that hold about `share` of the plan's
-    visibility-taps (sum of S^2), from the plan's own bins; 1..nw-1."""
+    """Number of low w planes whose share of the plan's visibility-taps (sum
+    of S^2) is nearest to `share`, from the plan's own bins; 1..nw-1."""
     import torch
     info = aw.aw_plan_query(plan)
     b = torch.empty(int(info.nvis), dtype=torch.int32, device="cuda")
@@ -1232,8 +1234,8 @@ def hybrid_split(aw, plan, kw, share: float) -> int:
     planes = (bins // per_plane) % kw["nw"]
     sup = torch.as_tensor(kw["supports"], dtype=torch.float64, device=bins.device)
     taps = torch.bincount(planes, weights=sup[planes] ** 2, minlength=kw["nw"]).cpu().numpy()
-    cum = np.cumsum(taps) / max(taps.sum(), 1.0)       # cum[q - 1]: share of planes < q
-    q = int(np.searchsorted(cum, share)) + 1
+    below = np.concatenate([[0.0], np.cumsum(taps) / max(taps.sum(), 1.0)])   # below[q]: share of planes < q
+    q = int(np.argmin(np.abs(below - share)))
     return max(1, min(q, kw["nw"] - 1))
 
 
