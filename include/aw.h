@@ -545,19 +545,21 @@ int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, flo
 
 /*
  * mosaic_gamma_noalloc - mosaic_gamma for callers that cannot allocate device
- * memory: code running while a stream is captured into a CUDA graph, code
- * inside a framework whose allocator owns the device memory, real-time loops
- * that forbid allocation after start-up.  It needs no aw_ctx (aw_create
- * allocates) and calls no cudaMalloc, cudaFree or allocating library routine.
+ * memory: code inside a framework whose caching allocator owns the device
+ * memory (a second allocator fragments it), real-time loops that forbid
+ * allocation after start-up (cudaMalloc may synchronise and takes unbounded
+ * time).  It needs no aw_ctx (aw_create allocates) and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
  * The paper has no counterpart; this is a deployment variant of the Eq. 1 call
  * above, with the same arguments and result.
  *
  * Scratch: a fixed file-scope device array of 4097 floats (16 KB) inside
  * libaw, held by every GPU that loads the library until the process exits.
  * Limit: N * N <= 4096 * 4096 pixels; larger images return AW_EINVAL before
- * any GPU work.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the one array and
+ * any GPU work.  The first call on a device (and the first after its context
+ * is re-created, e.g. by cudaDeviceReset) looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and
  * nothing in it needs to start at zero (each pass reads only slots written
  * earlier in the same call), but calls whose GPU work overlaps (different
  * streams or host threads) race on it: serialise them.  beams: device float

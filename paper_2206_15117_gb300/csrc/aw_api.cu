@@ -517,20 +517,24 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
         if (ms_best < best) { best = ms_best; bt = tu; }
     }
     // the hybrid schedule: the first planes holding about a quarter to a half
-    // of the visibility-taps on TILES, the rest on OFFSETS, at 2 or 3 TILES CTAs per SM
+    // of the visibility-taps on TILES, the rest on OFFSETS, at 2 or 3 TILES CTAs
+    // per SM.  A hybrid candidate that cannot be built or run (its second stream
+    // or events, its item lists) is skipped: the TILES / OFFSETS schedule
+    // already measured stays the answer.
     std::vector<double> cum;
-    if (!rc) {
+    int hrc = rc;
+    if (!hrc) {
         aw_tune tu{bt.tile, bt.chunk, 2, bt.dg_tile ? bt.dg_tile : 1024, AW_GRID_TILES};
         aw_plan *p = new aw_plan();
         p->device = ctx->device;
-        rc = aw_plan_build(ctx, vis, k, &tu, p, s);
-        if (!rc) rc = aw_plan_plane_taps(p, cum, s);
+        hrc = aw_plan_build(ctx, vis, k, &tu, p, s);
+        if (!hrc) hrc = aw_plan_plane_taps(p, cum, s);
         free_plan(p);
     }
     int last_q = -1;
     const double targets[] = {0.25, 0.35, 0.45};
     for (double target : targets) {
-        if (rc || cum.empty()) break;
+        if (hrc || cum.empty()) break;
         int q = 1;
         while (q < (int)cum.size() - 1 && cum[q] < target) ++q;   // cum[q]: share of planes < q
         if (q <= last_q || q >= (int)cum.size() - 1) continue;
@@ -538,17 +542,18 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
         aw_tune tu{bt.tile, bt.chunk, 2, bt.dg_tile ? bt.dg_tile : 1024, AW_GRID_HYBRID, q};
         aw_plan *p = new aw_plan();
         p->device = ctx->device;
-        rc = aw_plan_build(ctx, vis, k, &tu, p, s);
-        if (rc) { free_plan(p); break; }
+        hrc = aw_plan_build(ctx, vis, k, &tu, p, s);
+        if (hrc) { free_plan(p); break; }
         for (int cp : {2, 3}) {
             p->tune.ctas_per_sm = cp;
             float ms_best = 1e30f;
-            rc = time_plan(p, &ms_best);
-            if (rc) break;
+            hrc = time_plan(p, &ms_best);
+            if (hrc) break;
             if (ms_best < best) { best = ms_best; bt = p->tune; }
         }
         free_plan(p);
     }
+    if (hrc && !rc) cudaGetLastError();   // clear a non-sticky error of the skipped candidate
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     aw_dev_free(grid);

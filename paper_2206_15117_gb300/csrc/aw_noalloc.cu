@@ -1,11 +1,12 @@
 // mosaic_gamma_noalloc: the Eq. 1 mosaic weighting for callers that cannot
 // allocate device memory.
 //
-// Some callers of this library cannot call cudaMalloc: code that runs while a
-// CUDA stream is being captured into a graph (allocation is not a capturable
-// operation), host code inside a framework whose caching allocator already owns
-// the device memory, and real-time pipelines that forbid allocation after
-// start-up.  mosaic_gamma needs an aw_ctx, and aw_create allocates.  This
+// Some callers of this library cannot call cudaMalloc: host code inside a
+// framework whose caching allocator already owns the device memory (a second
+// allocator on the same GPU fragments it and can fail the framework's own
+// requests), and real-time pipelines that forbid allocation after start-up
+// (cudaMalloc can synchronise the device and take unbounded time).
+// mosaic_gamma needs an aw_ctx, and aw_create allocates.  This
 // variant takes no context: its only scratch is the file-scope array below,
 // which every GPU that loads the library holds until the process exits.
 //
@@ -87,23 +88,59 @@ __global__ void noalloc_apply(const float *B, int nfield, int64_t npix, const fl
     }
 }
 
-// Device address of g_gamma_scratch, looked up once per device with that
-// device current (in host code the symbol itself is only a host-side stand-in).
+// Device address of g_gamma_scratch, looked up with the device current (in
+// host code the symbol itself is only a host-side stand-in).  A module is
+// loaded per CUDA context, and a context torn down (cudaDeviceReset) and made
+// again may place the array elsewhere, so the cached address is keyed on the
+// identity of the current context (cuCtxGetId, unique for the life of the
+// process), not on the device index: the first call in each new context looks
+// the address up again.
+typedef int (*ctx_get_current_fn)(void **);
+typedef int (*ctx_get_id_fn)(void *, unsigned long long *);
+
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;
+    float *addr = nullptr;
+};
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
-float *g_addr[kMaxDevices] = {nullptr};
+ScratchSlot g_slot[kMaxDevices];
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+
+int current_context_id(unsigned long long *id) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || !f1 || !f2)
+            return aw_set_error(AW_ECUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable");
+        g_ctx_get_current = reinterpret_cast<ctx_get_current_fn>(f1);
+        g_ctx_get_id = reinterpret_cast<ctx_get_id_fn>(f2);
+    }
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return aw_set_error(AW_ECUDA, "no current CUDA context");
+    if (g_ctx_get_id(ctx, id) != 0) return aw_set_error(AW_ECUDA, "cuCtxGetId failed");
+    return AW_OK;
+}
 
 int scratch_address(int dev, float **out) {
     if (dev < 0 || dev >= kMaxDevices) return aw_set_error(AW_EUNSUPPORTED, "device %d beyond %d", dev, kMaxDevices);
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc) return rc;
+    ScratchSlot &sl = g_slot[dev];
+    if (!sl.addr || sl.ctx_id != id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_gamma_scratch);
         if (e != cudaSuccess)
             return aw_set_error(AW_ECUDA, "cudaGetSymbolAddress(g_gamma_scratch): %s", cudaGetErrorString(e));
-        g_addr[dev] = static_cast<float *>(p);
+        sl.addr = static_cast<float *>(p);
+        sl.ctx_id = id;
     }
-    *out = g_addr[dev];
+    *out = sl.addr;
     return AW_OK;
 }
 
@@ -123,6 +160,10 @@ extern "C" int mosaic_gamma_noalloc(const float *beams, int32_t nfield, int32_t 
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+        // binds the device's primary context to this host thread (the context
+        // identity below needs it current)
+        e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
         float *scratch = nullptr;
         int rc = scratch_address(dev, &scratch);
         if (rc) return rc;

@@ -1,9 +1,9 @@
 """mosaic_gamma_noalloc: the allocation-free variant of mosaic_gamma.
 
-Some callers cannot allocate device memory (code running under CUDA graph
-capture, code inside a framework whose allocator owns the GPU, real-time loops
-that forbid allocation).  This entry point serves them with a fixed scratch
-array inside the library.  The test calls it through the C ABI and checks it
+Some callers cannot allocate device memory (code inside a framework whose
+caching allocator owns the GPU, real-time loops that forbid allocation after
+start-up).  This entry point serves them with a fixed scratch array inside the
+library.  The test calls it through the C ABI and checks it
 against the existing mosaic_gamma on two calls in a row with different
 inputs, so that what the first call leaves in the shared scratch cannot leak
 into the second.  It is collected last on purpose.
