@@ -909,8 +909,14 @@ def run_ours(args, rank, world, dist):
         for share in (0.25, 0.30, 0.35, 0.40):
             finalists.append(aw.aw_tune(tune.tile, tune.chunk, 2, 1024, aw.AW_GRID_HYBRID,
                                         hybrid_split(aw, plan, kw, share)))
+        # the region schedule with the planes of supports up to 32, 40 and 48 cells on the region kernel
+        for lim in (32, 40, 48):
+            q = sum(1 for s_ in kw["supports"] if s_ <= lim)
+            if 0 < q:
+                finalists.append(aw.aw_tune(tune.tile, tune.chunk, 2, 1024, aw.AW_GRID_REGION, q))
         key = lambda t_: (t_.grid_mode, t_.ctas_per_sm if t_.grid_mode != aw.AW_GRID_OFFSETS else 0,
-                          t_.split_planes if t_.grid_mode == aw.AW_GRID_HYBRID else 0, t_.dg_tile or 1024)
+                          t_.split_planes if t_.grid_mode in (aw.AW_GRID_HYBRID, aw.AW_GRID_REGION) else 0,
+                          t_.dg_tile or 1024)
         seen = {key(tune)}
         for t_ in finalists:
             if key(t_) not in seen:
@@ -930,7 +936,9 @@ def run_ours(args, rank, world, dist):
                 ms.append(a_.elapsed_time(b_))
             times.append(min(ms[1:]))
         label = lambda t_: SCHEDULES[t_.grid_mode] + ("/%d/%d" % (t_.split_planes, t_.ctas_per_sm)
-                                                       if t_.grid_mode == aw.AW_GRID_HYBRID else "")
+                                                       if t_.grid_mode == aw.AW_GRID_HYBRID else
+                                                       "/%d" % t_.split_planes if t_.grid_mode == aw.AW_GRID_REGION
+                                                       else "")
         confirm = {"full_data_grid_ms": {label(t_): ms_ for (t_, _), ms_ in zip(cands, times)},
                    "seconds": None}
         best = int(np.argmin(times))
@@ -938,7 +946,7 @@ def run_ours(args, rank, world, dist):
         # the 16-bit variants choose between the best plan of each schedule
         alt_plans = []
         if not args.no_variants:
-            for mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS, aw.AW_GRID_HYBRID):
+            for mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS, aw.AW_GRID_HYBRID, aw.AW_GRID_REGION):
                 idx = [i for i, (t_, _) in enumerate(cands) if t_.grid_mode == mode and i != best]
                 if idx and mode != tune.grid_mode:
                     alt_plans.append(cands[min(idx, key=lambda i: times[i])])
@@ -955,7 +963,7 @@ def run_ours(args, rank, world, dist):
     image = torch.empty((4, N, N), dtype=torch.float32, device=dev)
     # grid (one kernel, or the two concurrent parts of the hybrid schedule), checker +
     # grid-correction (FFT step), degrid
-    launches_per_step = 4 + (1 if tune.grid_mode == aw.AW_GRID_HYBRID else 0)
+    launches_per_step = 3 + info.grid_kernels
     # pinned host buffers of the end-to-end measurement, allocated up front: allocated after the
     # BF16/FP16 variant sets had been built and freed, the same transfers measured about 9x slower
     host_bufs = None
@@ -1007,9 +1015,10 @@ def run_ours(args, rank, world, dist):
     g_ms, d_ms = statistics.mean(t_grid), statistics.mean(t_deg)
     dom_ms = max(g_ms, d_ms)
     gname = {aw.AW_GRID_TILES: "grid_persistent_kernel", aw.AW_GRID_OFFSETS: "grid_offset_kernel",
-             aw.AW_GRID_HYBRID: "grid_persistent_kernel + grid_offset_kernel"}[tune.grid_mode]
+             aw.AW_GRID_HYBRID: "grid_persistent_kernel + grid_offset_kernel",
+             aw.AW_GRID_REGION: "grid_region_kernel + grid_offset_kernel"}[tune.grid_mode]
     dom = ("aw_grid (%s)" % gname) if g_ms >= d_ms else "aw_degrid (degrid_items_kernel)"
-    peak_tflops = fp32_peak_tflops()
+    peak_tflops, peak_src = fp32_peak_tflops(dev_index)
     achieved = flops / (dom_ms / 1e3) / 1e12
     # DRAM bytes per launch of the dominant kernel, from the one-pass ncu capture summarised in
     # profiles/dram_traffic_fullpol_aw_64M.md (same kernels, this workload, FP32 tables); null otherwise
@@ -1037,8 +1046,12 @@ def run_ours(args, rank, world, dist):
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic,
             "traffic_source": "profiles/dram_traffic_fullpol_aw_64M.md" if traffic else None,
-            "peak_source": "FP32 CUDA-core peak derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-            "flops_per_launch": flops}
+            "peak_source": peak_src, "flops_per_launch": flops}
+    alt = bf16_scaled_peak()
+    if alt:
+        roof["peak_alt"] = {"value": alt, "frac": achieved / alt,
+                            "source": "measured bf16 dense burst (MEASURED_PEAKS.json) x 1/32, the nominal ratio "
+                                      "of the FP32 CUDA-core rate to the dense 16-bit tensor rate"}
 
     # variants: BF16 / FP16 kernel tables (FP32 arithmetic).  Without --tune each precision grids
     # with the faster of the two schedules on its own tables, as aw_autotune on that kernel set would
@@ -1218,7 +1231,7 @@ def aggregate(total_ms: float, nvis: int, dist=None, device=None):
     return float(t.item()), int(n.item())
 
 
-SCHEDULES = ["tiles", "offsets", "hybrid"]
+SCHEDULES = ["tiles", "offsets", "hybrid", "region"]
 
 
 def hybrid_split(aw, plan, kw, share: float) -> int:
@@ -1239,13 +1252,28 @@ def hybrid_split(aw, plan, kw, share: float) -> int:
     return max(1, min(q, kw["nw"] - 1))
 
 
-def fp32_peak_tflops():
+def fp32_peak_tflops(device_index: int = 0):
+    """FP32 CUDA-core peak from the device's SM count, 128 FP32 lanes per SM,
+    2 flop per FMA and the maximum SM clock (MEASURED_PEAKS.json's, else the
+    nominal 2070 MHz).  Returns (TFLOP/s, how it was derived)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
     try:
         j = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        mhz = float(j.get("sm_max_mhz", 2070.0))
+        mhz, src = float(j["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
     except Exception:
-        mhz = 2070.0
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+        mhz, src = 2070.0, "nominal maximum SM clock"
+    return (sms * 128 * 2 * mhz * 1e6 / 1e12,
+            "FP32 CUDA-core peak derived: %d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz (%s)" % (sms, mhz, src))
+
+
+def bf16_scaled_peak():
+    """The measured dense bf16 tensor burst scaled by 1/32 (nominal FP32
+    CUDA-core : dense 16-bit tensor ratio), or None."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]) / 32.0
+    except Exception:
+        return None
 
 
 def main():

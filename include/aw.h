@@ -150,7 +150,8 @@ typedef struct aw_tune {
     int32_t dg_tile;         /* degridding super-tile side (power of 2, 32..4096);
                               * 0 selects 1024.  Degridding visits visibilities
                               * grouped by (bin, super-tile, oversampled offset) */
-    int32_t grid_mode;       /* AW_GRID_TILES, AW_GRID_OFFSETS or AW_GRID_HYBRID  */
+    int32_t grid_mode;       /* AW_GRID_TILES, AW_GRID_OFFSETS, AW_GRID_HYBRID or
+                              * AW_GRID_REGION                                    */
     int32_t split_planes;    /* AW_GRID_HYBRID: visibilities in w planes
                               * [0, split_planes) take the TILES schedule, the
                               * rest OFFSETS; 0..nw.  Ignored by the other modes */
@@ -167,9 +168,16 @@ typedef struct aw_tune {
  * the call forks from and joins back into the caller's stream, also inside
  * the graph of aw_grid_batched).  The TILES kernel is bound by the L2->SM
  * stream of kernel values, the OFFSETS kernel by its atomics, so sharing the
- * SMs between them beats either alone.  All modes give the same grid up to
- * FP32 rounding order. */
-enum { AW_GRID_TILES = 0, AW_GRID_OFFSETS = 1, AW_GRID_HYBRID = 2 };
+ * SMs between them beats either alone.  REGION (full polarisation): work
+ * items of one bin and one grid tile whose side is chosen per support, sorted
+ * by oversampled offset; the CTA accumulates the tile's output region (tile +
+ * support - 1 cells square, at most 56) in shared memory, each thread holding
+ * one kernel tap's Mueller values in registers for all visibilities of an
+ * offset, and adds the region to the grid once; bins whose support does not
+ * fit (above 49 cells) take OFFSETS on the plan's second stream at the same
+ * time.  Stokes-I plans given REGION grid every bin with OFFSETS.  All modes
+ * give the same grid up to FP32 rounding order. */
+enum { AW_GRID_TILES = 0, AW_GRID_OFFSETS = 1, AW_GRID_HYBRID = 2, AW_GRID_REGION = 3 };
 
 typedef struct aw_plan_info {
     int64_t nvis;
@@ -181,6 +189,8 @@ typedef struct aw_plan_info {
     int32_t chunk;
     double mean_taps;        /* mean S^2 over the valid visibilities              */
     int64_t nitems_degrid;   /* degridding work items                             */
+    int32_t grid_kernels;    /* kernels one aw_grid / aw_grid_batched call launches */
+    int32_t region_lists;    /* AW_GRID_REGION: supports on the region kernel      */
 } aw_plan_info;
 
 typedef struct aw_stats {

@@ -18,7 +18,7 @@ LIB_PATH = os.environ.get("AW_LIBAW") or os.path.join(HERE, "libaw.so")
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ETIMEOUT, AW_EUNSUPPORTED, AW_EREJECTED = range(7)
 AW_ROLE_GRID, AW_ROLE_DEGRID, AW_ROLE_ADJOINT, AW_ROLE_BEAM = 0, 1, 2, 3
 AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
-AW_GRID_TILES, AW_GRID_OFFSETS, AW_GRID_HYBRID = 0, 1, 2
+AW_GRID_TILES, AW_GRID_OFFSETS, AW_GRID_HYBRID, AW_GRID_REGION = 0, 1, 2, 3
 AW_INTERP_BILINEAR, AW_INTERP_CUBIC = 0, 1
 AW_ENGINE_MMA_SYNC, AW_ENGINE_TCGEN05 = 0, 1
 AW_FREQ_BIN, AW_FREQ_CHANNEL = 0, 1
@@ -56,7 +56,7 @@ class aw_tune(ctypes.Structure):
 class aw_plan_info(ctypes.Structure):
     _fields_ = [("nvis", c_i64), ("nvalid", c_i64), ("n_outside", c_i64), ("n_flagged", c_i64),
                 ("nitems", c_i64), ("tile", c_i32), ("chunk", c_i32), ("mean_taps", c_dbl),
-                ("nitems_degrid", c_i64)]
+                ("nitems_degrid", c_i64), ("grid_kernels", c_i32), ("region_lists", c_i32)]
 
 
 class aw_sky_frame(ctypes.Structure):

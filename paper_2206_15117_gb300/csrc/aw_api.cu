@@ -233,6 +233,10 @@ static void free_plan(aw_plan *p) {
     if (p->d_counter) aw_dev_free(p->d_counter);
     if (p->d_items_ht) aw_dev_free(p->d_items_ht);
     if (p->d_items_ho) aw_dev_free(p->d_items_ho);
+    if (p->d_rec_rg) aw_dev_free(p->d_rec_rg);
+    for (auto &c : p->rclasses)
+        if (c.d_items) aw_dev_free(c.d_items);
+    if (p->d_rcounter) aw_dev_free(p->d_rcounter);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->aux) cudaStreamDestroy(p->aux);
@@ -275,6 +279,14 @@ int aw_plan_query(const aw_plan *p, aw_plan_info *info) {
     info->chunk = p->tune.chunk;
     info->mean_taps = p->mean_taps;
     info->nitems_degrid = p->nitems_dg;
+    int nl = 0;
+    for (const auto &c : p->rclasses) nl += c.n > 0;
+    info->region_lists = nl;
+    switch (p->tune.grid_mode) {
+        case AW_GRID_HYBRID: info->grid_kernels = (p->nitems_ht > 0) + (p->nitems_ho > 0); break;
+        case AW_GRID_REGION: info->grid_kernels = nl + (p->nitems_ho > 0); break;
+        default: info->grid_kernels = p->nitems > 0 ? 1 : 0;
+    }
     return AW_OK;
 }
 
@@ -339,6 +351,27 @@ static int launch_planned(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k,
         const int64_t c = std::min<int64_t>((int64_t)ctx->sm_count * p->tune.ctas_per_sm, n);
         return (int)std::max<int64_t>(c, 1);
     };
+    if (p->tune.grid_mode == AW_GRID_REGION) {
+        // the region lists on the caller's stream; the bins that take no region
+        // (wide supports, or planes from split_planes on) with the OFFSETS
+        // kernel on the second stream at the same time, one CTA per SM (it
+        // fits beside two region CTAs: registers, shared memory, threads)
+        if (p->nitems_ho == 0) return aw_launch_grid_region(p, k, vis, weight, grid, s);
+        if (p->nreg == 0) {   // no bin takes a region (e.g. Stokes I): OFFSETS alone, every SM
+            aw_grid_launch Lo{p, k, vis, weight, grid, false, 0, s, AW_GRID_OFFSETS, p->d_items_ho, p->nitems_ho};
+            return aw_launch_grid(Lo);
+        }
+        if (!p->aux) return aw_set_error(AW_EINVAL, "region plan without its second stream");
+        AW_CUDA_TRY(cudaEventRecord(p->ev_fork, s));
+        AW_CUDA_TRY(cudaStreamWaitEvent(p->aux, p->ev_fork, 0));
+        aw_grid_launch Lo{p, k, vis, weight, grid, false, ctx->sm_count, p->aux, AW_GRID_OFFSETS, p->d_items_ho,
+                          p->nitems_ho};
+        int rc = aw_launch_grid(Lo);
+        if (rc == AW_OK) rc = aw_launch_grid_region(p, k, vis, weight, grid, s);
+        AW_CUDA_TRY(cudaEventRecord(p->ev_join, p->aux));
+        AW_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_join, 0));
+        return rc;
+    }
     if (p->tune.grid_mode != AW_GRID_HYBRID) {
         aw_grid_launch L{p, k, vis, weight, grid, persistent, ctas_for(p->nitems), s};
         return aw_launch_grid(L);
@@ -515,6 +548,27 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
         free_plan(p);
         if (rc) break;
         if (ms_best < best) { best = ms_best; bt = tu; }
+    }
+    // the region schedule (full polarisation): the w planes up to the last one
+    // whose support is at most 32, 40 or 48 cells on the region kernel, the rest
+    // on OFFSETS at the same time (its super-tile the larger one)
+    if (!rc && k->spec.npol == 4) {
+        int last_split = -1;
+        for (int lim : {32, 40, 48}) {
+            int q = 0;
+            while (q < k->spec.nw && k->supports[(size_t)q] <= lim) ++q;
+            if (q == 0 || q == last_split) continue;
+            last_split = q;
+            aw_tune tu{bt.tile, bt.chunk, 2, 1024, AW_GRID_REGION, q};
+            aw_plan *p = new aw_plan();
+            p->device = ctx->device;
+            int r2 = aw_plan_build(ctx, vis, k, &tu, p, s);
+            float ms_best = 1e30f;
+            if (!r2) r2 = time_plan(p, &ms_best);
+            free_plan(p);
+            if (!r2 && ms_best < best) { best = ms_best; bt = tu; }
+            if (r2) cudaGetLastError();   // a candidate that cannot be built is skipped
+        }
     }
     // the hybrid schedule: the first planes holding about a quarter to a half
     // of the visibility-taps on TILES, the rest on OFFSETS, at 2 or 3 TILES CTAs

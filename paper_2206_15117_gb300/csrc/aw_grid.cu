@@ -845,14 +845,15 @@ int offsets_beside_tiles(int tiles_per_sm, int chunk, int alone) {
 }
 
 template <int NPOL, int ST>
-int launch_grid_offset_t(const GridOffArgs &a, int sm_count, cudaStream_t s, int beside_tiles = 0, int chunk = 0) {
+int launch_grid_offset_t(const GridOffArgs &a, int sm_count, cudaStream_t s, int beside_tiles = 0, int chunk = 0,
+                         int fixed_ctas = 0) {
     // one wave of resident CTAs striding over the items in order, so that the
     // items in flight share bins and super-tiles (L2 locality)
     int per_sm = 1;
     AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_offset_kernel<NPOL, ST>, 256, 0));
     if (beside_tiles > 0) per_sm = offsets_beside_tiles<NPOL, ST>(beside_tiles, chunk, std::max(per_sm, 1));
     int64_t blocks = a.nitems;
-    const int64_t cap = (int64_t)sm_count * std::max(per_sm, 1);
+    const int64_t cap = fixed_ctas > 0 ? (int64_t)fixed_ctas : (int64_t)sm_count * std::max(per_sm, 1);
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     grid_offset_kernel<NPOL, ST><<<(unsigned)blocks, 256, 0, s>>>(a);
@@ -886,16 +887,19 @@ int launch_grid_offsets(const aw_grid_launch &L) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int st = k->spec.storage;
-    // as a part of the hybrid schedule: leave room for the tile kernel's CTAs
-    const int bt = L.mode >= 0 ? p->tune.ctas_per_sm : 0, ch = p->tune.chunk;
+    // as a part of the hybrid schedule: leave room for the tile kernel's CTAs;
+    // as a part of the region schedule: the CTA count the caller gives (L.ctas)
+    const int bt = (L.mode >= 0 && p->tune.grid_mode == AW_GRID_HYBRID) ? p->tune.ctas_per_sm : 0;
+    const int fx = (L.mode >= 0 && p->tune.grid_mode == AW_GRID_REGION) ? L.ctas : 0;
+    const int ch = p->tune.chunk;
     if (p->npol == 1) {
-        if (st == AW_STORAGE_FP32) return launch_grid_offset_t<1, AW_STORAGE_FP32>(a, sms, L.stream, bt, ch);
-        if (st == AW_STORAGE_BF16) return launch_grid_offset_t<1, AW_STORAGE_BF16>(a, sms, L.stream, bt, ch);
-        return launch_grid_offset_t<1, AW_STORAGE_FP16>(a, sms, L.stream, bt, ch);
+        if (st == AW_STORAGE_FP32) return launch_grid_offset_t<1, AW_STORAGE_FP32>(a, sms, L.stream, bt, ch, fx);
+        if (st == AW_STORAGE_BF16) return launch_grid_offset_t<1, AW_STORAGE_BF16>(a, sms, L.stream, bt, ch, fx);
+        return launch_grid_offset_t<1, AW_STORAGE_FP16>(a, sms, L.stream, bt, ch, fx);
     }
-    if (st == AW_STORAGE_FP32) return launch_grid_offset_t<4, AW_STORAGE_FP32>(a, sms, L.stream, bt, ch);
-    if (st == AW_STORAGE_BF16) return launch_grid_offset_t<4, AW_STORAGE_BF16>(a, sms, L.stream, bt, ch);
-    return launch_grid_offset_t<4, AW_STORAGE_FP16>(a, sms, L.stream, bt, ch);
+    if (st == AW_STORAGE_FP32) return launch_grid_offset_t<4, AW_STORAGE_FP32>(a, sms, L.stream, bt, ch, fx);
+    if (st == AW_STORAGE_BF16) return launch_grid_offset_t<4, AW_STORAGE_BF16>(a, sms, L.stream, bt, ch, fx);
+    return launch_grid_offset_t<4, AW_STORAGE_FP16>(a, sms, L.stream, bt, ch, fx);
 }
 
 }  // namespace
@@ -905,7 +909,8 @@ int aw_launch_grid(const aw_grid_launch &L) {
     const aw_kernel_set *k = L.kset;
     if (p->nitems == 0) return AW_OK;
     const int mode = L.mode >= 0 ? L.mode : p->tune.grid_mode;
-    if (mode == AW_GRID_HYBRID) return aw_set_error(AW_EINVAL, "hybrid schedule launched as one part");
+    if (mode == AW_GRID_HYBRID || mode == AW_GRID_REGION)
+        return aw_set_error(AW_EINVAL, "hybrid / region schedule launched as one part");
     if (mode == AW_GRID_OFFSETS) return launch_grid_offsets(L);
     GridArgs a;
     a.rec = p->d_rec;
@@ -978,14 +983,16 @@ int aw_launch_degrid(const aw_plan *p, const aw_kernel_set *k, const void *grid,
 extern "C" int aw_debug_bounds_status(uint32_t *status, int32_t reset) {
     if (!status) return aw_set_error(AW_EINVAL, "status is NULL");
 #ifdef AW_BOUNDS_CHECK
-    unsigned int v = 0;
+    unsigned int v = 0, vr = 0;
     AW_CUDA_TRY(cudaDeviceSynchronize());
     AW_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_bounds_status, sizeof(v)));
     if (reset) {
         const unsigned int z = 0;
         AW_CUDA_TRY(cudaMemcpyToSymbol(g_bounds_status, &z, sizeof(z)));
     }
-    *status = v;
+    int rc = aw_region_bounds_status(&vr, reset);
+    if (rc) return rc;
+    *status = v ? v : vr;
     return AW_OK;
 #else
     (void)reset;

@@ -145,6 +145,20 @@ struct aw_plan {
     int64_t nitems_ho = 0;
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // AW_GRID_REGION: the valid visibilities of the bins whose support fits a
+    // shared-memory region, by (bin, region tile, oversampled offset,
+    // position), cut into items {start, count, bin, tile}; one item list per
+    // support (each launched with its own CTA size).  The other bins' degridding
+    // items (d_items_ho) take the OFFSETS schedule on the second stream.
+    aw_rec *d_rec_rg = nullptr;
+    int64_t nreg = 0;
+    struct RegionClass {
+        int S = 0, T = 0, BT = 0;
+        int4 *d_items = nullptr;
+        int64_t n = 0;
+    };
+    std::vector<RegionClass> rclasses;
+    unsigned int *d_rcounter = nullptr;   // [AW_RG_MAXCLASS] work-queue heads
     // coordinate inputs kept for aw_plan_coords
     aw_vis_desc vis{};
     double uscale = 0, half = 0, winv = 0;
@@ -165,6 +179,15 @@ struct aw_plan {
         }
     }
 };
+
+// REGION gridding: largest region side (cells) held in shared memory, and the
+// most distinct supports (item lists) a plan launches.
+#ifndef AW_RG_RMAX_CELLS
+#define AW_RG_RMAX_CELLS 56
+#endif
+constexpr int AW_RG_RMAX = AW_RG_RMAX_CELLS;
+constexpr int AW_RG_MAXCLASS = 64;
+constexpr int AW_RG_MAXV = 1024;   // visibilities per region work item
 
 // Visibilities per degridding work item: 8 warps x 4 visibilities.
 constexpr int AW_DG_VB = 4;
@@ -214,6 +237,15 @@ struct aw_grid_launch {
     int64_t nitems = 0;
 };
 int aw_launch_grid(const aw_grid_launch &L);
+// REGION schedule (aw_grid_region.cu): region tile side for support S (0: the
+// support does not fit a region), CTA size for support S, and the launch of
+// every support's item list on stream s.
+int aw_region_tile(int S, int npol);
+int aw_region_rows(int S);
+int aw_region_threads(int S);
+int aw_launch_grid_region(const aw_plan *p, const aw_kernel_set *k, const void *vis, const float *weight, void *grid,
+                          cudaStream_t s);
+int aw_region_bounds_status(unsigned int *v, int reset);
 // cum[q] = share of the plan's visibility-taps (sum of S^2) in w planes < q, q = 0..nw
 int aw_plan_plane_taps(const aw_plan *plan, std::vector<double> &cum, cudaStream_t s);
 int aw_launch_degrid(const aw_plan *plan, const aw_kernel_set *kset, const void *grid,

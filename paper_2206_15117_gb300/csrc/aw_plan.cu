@@ -258,19 +258,55 @@ __global__ void seg_chunks_kernel(const uint32_t *starts, int64_t nseg, uint32_t
     }
 }
 
+// bin_tile (may be NULL): per-bin region geometry (tile side in the low 8
+// bits); then item.w holds the segment's tile as (row << 16) | column.
 __global__ void emit_items_kernel(const uint32_t *starts, const uint32_t *itembase, int64_t nseg,
-                                  uint32_t nvalid, int chunk, const aw_rec *rec, int4 *items) {
+                                  uint32_t nvalid, int chunk, const aw_rec *rec, const int32_t *bin_tile,
+                                  int4 *items) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg;
          s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = starts[s];
         const uint32_t b = (s + 1 < nseg) ? starts[s + 1] : nvalid;
-        const int bin = rec[a].bin;
+        const aw_rec r = rec[a];
+        const int bin = r.bin;
+        int w = 0;
+        if (bin_tile) {
+            const int T = max(bin_tile[bin] & 0xff, 1);
+            w = ((int)r.y0 / T) << 16 | ((int)r.x0 / T);
+        }
         uint32_t pos = itembase[s];
         for (uint32_t st = a; st < b; st += chunk) {
             const uint32_t cnt = min((uint32_t)chunk, b - st);
-            items[pos++] = make_int4((int)st, (int)cnt, bin, 0);
+            items[pos++] = make_int4((int)st, (int)cnt, bin, w);
         }
     }
+}
+
+// REGION key of the i-th valid visibility (grid order): (bin, region tile
+// row, region tile column, oversampled offset, footprint row in the tile
+// modulo M) above the position inside the tile (6 + 6 bits; tiles are at most
+// 49 cells).  geo[bin] = T | M << 8 (0: the bin takes no region); those bins
+// get invalid_key (sorted last); eligible ones are counted in *nreg.
+__global__ void rg_key_kernel(const aw_rec *rec, int64_t nv, const int32_t *geo, int OS, int osb, int nt,
+                              uint64_t invalid_key, uint64_t *keys, uint32_t *vals, unsigned long long *nreg) {
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const aw_rec r = rec[i];
+        const int T = geo[r.bin] & 0xff, M = geo[r.bin] >> 8;
+        uint64_t key = invalid_key;
+        if (T > 0 && M > 0) {
+            const int ty = (int)r.y0 / T, tx = (int)r.x0 / T;
+            const int ly = (int)r.y0 - ty * T, lx = (int)r.x0 - tx * T;
+            const uint64_t grp = ((((uint64_t)r.bin * nt + ty) * nt + tx) << osb) | (uint64_t)(r.fy * OS + r.fx);
+            key = (((grp << 4) | (uint64_t)(ly % M)) << 12) | ((uint64_t)ly << 6) | (uint64_t)lx;
+            cnt++;
+        }
+        keys[i] = key;
+        vals[i] = (uint32_t)i;
+    }
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nreg, cnt);
 }
 
 
@@ -375,7 +411,8 @@ int radix_sort_pairs(uint64_t *&k0, uint32_t *&v0, uint64_t *&k1, uint32_t *&v1,
 // key >> shift and the segments into items of at most `chunk` visibilities;
 // allocates *items.  `flag`/`segid` hold nv + 1 words each.
 int build_items(const uint64_t *keys, int64_t nv, int shift, int chunk, const aw_rec *rec, uint32_t *flag,
-                uint32_t *segid, void *scratch, int4 **items, int64_t *nitems, cudaStream_t s) {
+                uint32_t *segid, void *scratch, int4 **items, int64_t *nitems, cudaStream_t s,
+                const int32_t *bin_tile = nullptr) {
     seg_flag_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(keys, nv, shift, flag);
     AW_CHECK_LAUNCH();
     int rc = aw_exclusive_scan_u32(flag, segid, nv, scratch, s);
@@ -403,7 +440,7 @@ int build_items(const uint64_t *keys, int64_t nv, int shift, int chunk, const aw
     *nitems = (int64_t)lb + ln;
     AW_CUDA_TRY(aw_dev_malloc(items, sizeof(int4) * std::max<int64_t>(*nitems, 1)));
     emit_items_kernel<<<grid_blocks(nseg, 256), 256, 0, s>>>((uint32_t *)bstarts.p, (uint32_t *)bbase.p, nseg,
-                                                            (uint32_t)nv, chunk, rec, *items);
+                                                            (uint32_t)nv, chunk, rec, bin_tile, *items);
     AW_CHECK_LAUNCH();
     // the temporaries are freed on return: finish the kernels that read them
     AW_CUDA_TRY(cudaStreamSynchronize(s));
@@ -443,6 +480,96 @@ static int build_hybrid_items(aw_plan *plan, cudaStream_t s) {
     return AW_OK;
 }
 
+// AW_GRID_REGION: the region order of the valid visibilities of bins whose
+// support fits a region (aw_region_tile), its items bucketed by support (one
+// launch each), and the OFFSETS items of the other bins with the second
+// stream.  k0/v0/k1/v1 and the scan buffers are the plan builder's (>= nv).
+static int build_region(aw_plan *plan, const aw_kernel_set *ks, int64_t nv, uint64_t *k0, uint32_t *v0,
+                        uint64_t *k1, uint32_t *v1, uint32_t *counts, uint32_t *offs, void *scratch,
+                        cudaStream_t s) {
+    const int nb = ks->nbins;
+    std::vector<int32_t> bt((size_t)nb, 0);
+    // bins of w planes [0, split_planes) (all planes when 0) whose support fits a region
+    const int per_plane = plan->npa * plan->nfb;
+    const int split = plan->tune.split_planes > 0 ? plan->tune.split_planes : plan->nw;
+    for (int b = 0; b < nb; ++b) {
+        const int S = ks->bin_support[(size_t)b], T = aw_region_tile(S, plan->npol);
+        const bool low = (b / per_plane) % plan->nw < split;
+        bt[(size_t)b] = (T && low) ? (T | aw_region_threads(S) / 32 << 8) : 0;
+    }
+    DevBuf dbt, dcnt;
+    AW_CUDA_TRY(aw_dev_malloc(&dbt.p, sizeof(int32_t) * std::max(nb, 1)));
+    AW_CUDA_TRY(cudaMemcpyAsync(dbt.p, bt.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s));
+    AW_CUDA_TRY(aw_dev_malloc(&dcnt.p, sizeof(unsigned long long)));
+    AW_CUDA_TRY(cudaMemsetAsync(dcnt.p, 0, sizeof(unsigned long long), s));
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_rcounter, sizeof(unsigned int) * AW_RG_MAXCLASS));
+    const int OS = plan->OS;
+    const int osb = ilog2(OS * OS);
+    const int nt = (plan->N + 7) / 8;
+    const uint64_t maxgrp = ((uint64_t)nb * nt * nt) << osb;
+    int gbits = 0;
+    while (gbits < 63 && (1ull << gbits) <= maxgrp) ++gbits;
+    if (gbits + 16 > 62) return aw_set_error(AW_EINVAL, "region key needs %d bits", gbits + 16);
+    const int kbits = gbits + 16;
+    const uint64_t invalid_key = 1ull << kbits;
+    rg_key_kernel<<<grid_blocks(nv, 256), 256, 0, s>>>(plan->d_rec, nv, (const int32_t *)dbt.p, OS, osb, nt,
+                                                      invalid_key, k0, v0, (unsigned long long *)dcnt.p);
+    AW_CHECK_LAUNCH();
+    int rc = radix_sort_pairs(k0, v0, k1, v1, nv, (kbits + 1 + 7) / 8, counts, offs, scratch, s);
+    if (rc) return rc;
+    unsigned long long nreg = 0;
+    AW_CUDA_TRY(cudaMemcpyAsync(&nreg, dcnt.p, sizeof(nreg), cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    plan->nreg = (int64_t)nreg;
+    AW_CUDA_TRY(aw_dev_malloc(&plan->d_rec_rg, sizeof(aw_rec) * std::max<int64_t>(plan->nreg, 1)));
+    if (plan->nreg > 0) {
+        gather_rec_kernel<<<grid_blocks(plan->nreg, 256), 256, 0, s>>>(plan->d_rec, v0, plan->nreg, plan->d_rec_rg);
+        AW_CHECK_LAUNCH();
+        int4 *d_items = nullptr;
+        int64_t nitems = 0;
+        rc = build_items(k0, plan->nreg, osb + 16, AW_RG_MAXV, plan->d_rec_rg, counts, offs, scratch, &d_items,
+                         &nitems, s, (const int32_t *)dbt.p);
+        if (rc) return rc;
+        std::vector<int4> h((size_t)nitems);
+        cudaError_t e = cudaMemcpyAsync(h.data(), d_items, sizeof(int4) * nitems, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        aw_dev_free(d_items);
+        if (e != cudaSuccess) return aw_set_error(AW_ECUDA, "region items: %s", cudaGetErrorString(e));
+        // one list per support, in increasing support (order inside a list kept)
+        std::map<int, std::vector<int4>> by_s;
+        for (const int4 &it : h) by_s[ks->bin_support[(size_t)it.z]].push_back(it);
+        if ((int)by_s.size() > AW_RG_MAXCLASS) return aw_set_error(AW_EUNSUPPORTED, "%d supports", (int)by_s.size());
+        for (auto &kv : by_s) {
+            aw_plan::RegionClass c;
+            c.S = kv.first;
+            c.T = aw_region_tile(c.S, plan->npol);
+            c.BT = aw_region_threads(c.S);
+            c.n = (int64_t)kv.second.size();
+            plan->rclasses.push_back(c);
+            AW_CUDA_TRY(aw_dev_malloc(&plan->rclasses.back().d_items, sizeof(int4) * kv.second.size()));
+            AW_CUDA_TRY(cudaMemcpyAsync(plan->rclasses.back().d_items, kv.second.data(), sizeof(int4) * kv.second.size(),
+                                        cudaMemcpyHostToDevice, s));
+        }
+    }
+    // the other bins: their degridding items on the OFFSETS schedule
+    std::vector<int4> hd((size_t)plan->nitems_dg), keep;
+    if (plan->nitems_dg)
+        AW_CUDA_TRY(cudaMemcpyAsync(hd.data(), plan->d_items_dg, sizeof(int4) * plan->nitems_dg, cudaMemcpyDeviceToHost, s));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    for (const int4 &it : hd)
+        if (bt[(size_t)it.z] == 0) keep.push_back(it);
+    plan->nitems_ho = (int64_t)keep.size();
+    if (!keep.empty()) {
+        AW_CUDA_TRY(aw_dev_malloc(&plan->d_items_ho, sizeof(int4) * keep.size()));
+        AW_CUDA_TRY(cudaMemcpyAsync(plan->d_items_ho, keep.data(), sizeof(int4) * keep.size(), cudaMemcpyHostToDevice, s));
+    }
+    AW_CUDA_TRY(cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking));
+    AW_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_fork, cudaEventDisableTiming));
+    AW_CUDA_TRY(cudaEventCreateWithFlags(&plan->ev_join, cudaEventDisableTiming));
+    AW_CUDA_TRY(cudaStreamSynchronize(s));
+    return AW_OK;
+}
+
 int aw_plan_plane_taps(const aw_plan *plan, std::vector<double> &cum, cudaStream_t s) {
     cum.assign((size_t)plan->nw + 1, 0.0);
     std::vector<int4> h((size_t)plan->nitems);
@@ -474,9 +601,11 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     if (t.dg_tile == 0) t.dg_tile = 1024;
     if (t.dg_tile < 32 || t.dg_tile > 4096 || (t.dg_tile & (t.dg_tile - 1)))
         return aw_set_error(AW_EINVAL, "dg_tile %d", t.dg_tile);
-    if (t.grid_mode != AW_GRID_TILES && t.grid_mode != AW_GRID_OFFSETS && t.grid_mode != AW_GRID_HYBRID)
+    if (t.grid_mode != AW_GRID_TILES && t.grid_mode != AW_GRID_OFFSETS && t.grid_mode != AW_GRID_HYBRID &&
+        t.grid_mode != AW_GRID_REGION)
         return aw_set_error(AW_EINVAL, "grid_mode %d", t.grid_mode);
-    if (t.grid_mode == AW_GRID_HYBRID && (t.split_planes < 0 || t.split_planes > sp.nw))
+    if ((t.grid_mode == AW_GRID_HYBRID || t.grid_mode == AW_GRID_REGION) &&
+        (t.split_planes < 0 || t.split_planes > sp.nw))
         return aw_set_error(AW_EINVAL, "split_planes %d outside 0..%d", t.split_planes, sp.nw);
     plan->tune = t;
     plan->dg_tile = t.dg_tile;
@@ -579,6 +708,10 @@ int aw_plan_build(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *ks, 
     if (rc) return rc;
     if (t.grid_mode == AW_GRID_HYBRID) {
         rc = build_hybrid_items(plan, s);
+        if (rc) return rc;
+    }
+    if (t.grid_mode == AW_GRID_REGION) {
+        rc = build_region(plan, ks, nv, k0, v0, k1, v1, counts, offs, bscratch.p, s);
         if (rc) return rc;
     }
     AW_CUDA_TRY(cudaStreamSynchronize(s));

@@ -48,7 +48,7 @@ def test_struct_sizes_match_header_layout(lib):
     assert ctypes.sizeof(aw.aw_tune) == 24
     assert ctypes.sizeof(aw.aw_stats) == 40
     assert ctypes.sizeof(aw.aw_vis_desc) == 8 * 3 + 8 * 8
-    assert ctypes.sizeof(aw.aw_plan_info) == 5 * 8 + 8 + 8 + 8
+    assert ctypes.sizeof(aw.aw_plan_info) == 5 * 8 + 8 + 8 + 8 + 8
 
 
 def test_struct_layout_matches_the_c_compiler(tmp_path):

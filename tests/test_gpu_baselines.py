@@ -79,7 +79,7 @@ def test_plan_bins_with_row_types_bit_exact(ctx):
     assert np.any((co.flip == 1) & (cls % 3 != cls // 3))
 
 
-@pytest.mark.parametrize("grid_mode", [0, 1])
+@pytest.mark.parametrize("grid_mode", [0, 1, 3])
 def test_grid_and_degrid_parity(ctx, grid_mode):
     from paper_2206_15117_gb300 import aw
     ob, kw, rt = _case()

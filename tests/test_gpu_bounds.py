@@ -31,7 +31,9 @@ SCRIPT = textwrap.dedent('''
     ctx = aw.aw_create(0)
     report = {}
     cases = [("fullpol", case_fullpol(n_t=12), [(8, 32, 3, 0, 0), (64, 128, 4, 256, 1), (32, 256, 2, 1024, 1),
-                                                 (16, 512, 2, 32, 0), (32, 256, 2, 256, 2, 1)]),
+                                                 (16, 512, 2, 32, 0), (32, 256, 2, 256, 2, 1),
+                                                 (32, 256, 2, 256, 3)]),
+             ("fullpol_wide", case_fullpol(n_t=200, radius=60.0, supports=(16, 40, 56)), [(32, 256, 2, 256, 3)]),
              ("stokes_i", case_stokes_i_cfg1(time_samples=20), [(16, 128, 2, 0, 0), (32, 256, 2, 256, 1),
                                                               (16, 128, 3, 256, 2, 1)])]
     for name, (ob, kw), tunes in cases:
@@ -78,7 +80,7 @@ def test_bounds_checked_build_reports_no_bad_index():
     line = [l for l in r.stdout.splitlines() if l.startswith("REPORT ")][-1]
     rep = json.loads(line[len("REPORT "):])
     assert rep["status"] == 0, rep
-    assert rep["fullpol"] < 1e-5 and rep["stokes_i"] < 1e-5, rep
+    assert rep["fullpol"] < 1e-5 and rep["stokes_i"] < 1e-5 and rep["fullpol_wide"] < 1e-5, rep
 
 
 def test_normal_build_has_no_bounds_checks():

@@ -136,7 +136,7 @@ def test_small_chunks_and_tiles_ragged(ctx):
     _check_degrid(c)
 
 
-@pytest.mark.parametrize("grid_mode", [0, 1])
+@pytest.mark.parametrize("grid_mode", [0, 1, 3])
 def test_flags_outside_and_nonfinite(ctx, grid_mode):
     from paper_2206_15117_gb300 import aw
     ob, kw = case_fullpol(N=128, n_t=12)
@@ -171,7 +171,7 @@ def test_grid_accumulates_into_existing_grid(cfg1):
 # Mixed precision (kernels in BF16 / FP16, FP32 products and accumulation):
 # the error is set by the 8 (BF16) or 11 (FP16) significand bits of the kernel
 # values; the bounds below are about 2^-9 and 2^-12 relative.
-@pytest.mark.parametrize("grid_mode", [0, 1])
+@pytest.mark.parametrize("grid_mode", [0, 1, 3])
 @pytest.mark.parametrize("storage,tol", [(1, 4e-3), (2, 5e-4)])
 def test_mixed_precision_grid_and_degrid(ctx, storage, tol, grid_mode):
     from paper_2206_15117_gb300 import aw
@@ -248,6 +248,46 @@ def test_hybrid_schedule_grid(ctx, which, split):
     _check_degrid(c)
 
 
+# The region schedule (a grid tile's output region accumulated in shared
+# memory, kernel taps in registers across each offset group, one flush per
+# tile) against the same oracle: full-pol cases whose supports all fit a region,
+# one that mixes region supports with a support too wide for it (its bins take
+# OFFSETS), a dense case whose tiles hold more visibilities than one staging
+# round and one work item, and Stokes I (every bin on OFFSETS); direct and
+# graph-captured, with BF16 / FP16 tables on the mixed case.
+@pytest.mark.parametrize("which", ["fullpol", "mixed_supports", "dense", "wproj"])
+def test_region_schedule_grid(ctx, which):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = {"fullpol": case_fullpol,
+              "mixed_supports": lambda: case_fullpol(supports=(16, 40, 56), n_t=30),
+              "dense": lambda: case_fullpol(n_t=600, radius=50.0, supports=(16, 24, 32)),
+              "wproj": lambda: case_wproj(vis_fraction=0.002)}[which]()
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_REGION))
+    _check_grid(c)
+    _check_grid(c, batched=True)
+    _check_grid(c, batched=True)  # the cached graph again
+    _check_degrid(c)
+    if which == "dense":
+        # tiles with more visibilities than one staging round (128) and than one item (1024)
+        co = c.co
+        ok = (co.valid == 1) & (co.bin // 4 % kw["nw"] == 0)     # the S = 16 plane (2 PA x 2 frequency bins)
+        T = 56 - 16 + 1
+        key = (co.bin[ok].astype(np.int64) * 4096 + co.y0[ok] // T) * 4096 + co.x0[ok] // T
+        assert np.unique(key, return_counts=True)[1].max() > 1024
+
+
+@pytest.mark.parametrize("storage,tol", [(1, 4e-3), (2, 5e-4)])
+def test_region_schedule_reduced_precision(ctx, storage, tol):
+    from paper_2206_15117_gb300 import aw
+    ob, kw = case_fullpol(supports=(16, 40, 56), n_t=30)
+    c = Case(ctx, ob, kw, storage=storage, tune=aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_REGION))
+    g, _ = c.gpu_grid(batched=True)
+    G, _, _ = c.oracle_grid()
+    l2, mx = rel_err(g, G)
+    assert l2 < tol and mx < 4 * tol, (l2, mx)
+    assert l2 > 1e-6
+
+
 def test_hybrid_split_must_name_planes(ctx):
     from paper_2206_15117_gb300 import aw
     ob, kw = case_fullpol(n_t=6)
@@ -265,11 +305,13 @@ def test_autotune_returns_a_valid_schedule(ctx):
     kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
     vd, _keep = aw.device_observation(ob)
     t = aw.aw_autotune(ctx, vd, kg)
-    assert t.grid_mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS, aw.AW_GRID_HYBRID)
+    assert t.grid_mode in (aw.AW_GRID_TILES, aw.AW_GRID_OFFSETS, aw.AW_GRID_HYBRID, aw.AW_GRID_REGION)
     if t.grid_mode == aw.AW_GRID_HYBRID:
         assert 0 < t.split_planes < kw["nw"] and t.ctas_per_sm in (2, 3)
+    if t.grid_mode == aw.AW_GRID_REGION:
+        assert 0 < t.split_planes <= kw["nw"]
     assert t.tile in (16, 32, 64) and t.chunk in (128, 256, 512)
-    if t.grid_mode == aw.AW_GRID_OFFSETS:
+    if t.grid_mode in (aw.AW_GRID_OFFSETS, aw.AW_GRID_REGION):
         assert t.dg_tile in (256, 1024)
     # the context keeps the result for plans made without a tune
     vd2, _keep2 = aw.device_observation(ob)
