@@ -49,18 +49,20 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 table variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--subset", action="store_true",
                     help="profiling case: only the visibilities of one (PA, frequency) bin pair, with its "
                          "32 w-plane kernels (same per-bin density and tables, 1/32 of the memory)")
     ap.add_argument("--tune", default=None, help="tile,chunk,ctas_per_sm[,dg_tile[,grid_mode]] (skips the autotuner)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-surrogate comparison")
     ap.add_argument("--no-learned-degrid", action="store_true", help="skip the learned degridding comparison")
+    ap.add_argument("--no-learned-full", action="store_true",
+                    help="skip the full configuration-5 mosaic (7 fields x 10M visibilities)")
     ap.add_argument("--learned-inline-case", type=int, default=None, metavar="ENGINE",
                     help="only run the small inline-surrogate profiling case on engine 0 (mma.sync) or 1 (tcgen05)")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
     ap.add_argument("--no-mosaic", action="store_true", help="skip the mosaic measurements")
     ap.add_argument("--no-baselines", action="store_true", help="skip the per-baseline kernel measurement")
+    ap.add_argument("--no-wproj", action="store_true", help="skip the configuration 2 / 4 measurement")
     ap.add_argument("--uvmosaic-fraction", type=float, default=0.1,
                     help="fraction of each mosaic field's visibilities in the UV/image-domain comparison")
     ap.add_argument("--clean-major", type=int, default=3, help="major cycles of the cleaning measurement")
@@ -139,9 +141,16 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
-def oracle_sample(ob, kw, cpu_seconds: float, seed: int = 5):
-    """A bounded sample of the workload for the FP64 oracle: every visibility
-    of a few seeded bins (capped), with the oracle's own kernels for them."""
+# Size of the oracle's sample of the workload: complex MACs of one grid +
+# degrid pass (about 16 s on one Grace core, 1 s on 16).  Fixed, so that the
+# cpu_baseline leg and the reference arm time the same visibilities.
+ORACLE_SAMPLE_MACS = 1.1e10
+
+
+def oracle_sample(ob, kw, budget_macs: float = ORACLE_SAMPLE_MACS, seed: int = 5):
+    """A fixed sample of the workload for the FP64 oracle: every visibility
+    of four seeded bins (each capped at a quarter of the MAC budget), with the
+    oracle's own kernels for them."""
     from oracle import core as oc
     from paper_2206_15117_gb300 import synthetic as sy
     rng = np.random.default_rng(seed)
@@ -157,9 +166,7 @@ def oracle_sample(ob, kw, cpu_seconds: float, seed: int = 5):
     # every visibility of the picked bins: the rows/channels of their (PA, frequency)
     # bin pairs, then the oracle's own coordinates
     sel = []
-    # grid + degrid cost ~ 2 x 16 S^2 complex MACs per visibility; the FP64 C loops of the oracle
-    # run about 0.7e9 of them per second on one Grace core (measured)
-    budget_macs = cpu_seconds * 0.7e9
+    # grid + degrid cost 2 x 16 S^2 complex MACs per visibility
     for b in pick:
         a_, f_ = (b // spec.nfb) % spec.npa, b % spec.nfb
         cand = np.flatnonzero((ob.pa_bin[ob.row_of_vis] == a_) & (ob.fbin[ob.chan_of_vis] == f_))
@@ -226,9 +233,13 @@ def oracle_mvis(smp, seconds):
     return smp["n"] / seconds / 1e6 * smp["S2_sample"] / smp["S2_all"]
 
 
+def oracle_mvis_unscaled(smp, seconds):
+    return smp["n"] / seconds / 1e6
+
+
 def sample_text(smp, threads=1):
-    return ("%d visibilities of bins %s of the same workload (mean S^2 %.0f vs %.0f for all); "
-            "Mvis/s scaled by that S^2 ratio; FP64 C loops, %s" %
+    return ("fixed sample: %d visibilities of bins %s of the same workload (mean S^2 %.0f vs %.0f for all); "
+            "value scaled by that S^2 ratio, value_sample_unscaled the sample's own rate; FP64 C loops, %s" %
             (smp["n"], smp["bins"], smp["S2_sample"], smp["S2_all"],
              "one thread" if threads == 1 else "%d threads on disjoint shards of the sample" % threads))
 
@@ -239,10 +250,9 @@ def run_reference(args, rank, world):
     from oracle import build as ob_build
     ob_build.build()
     ob, kw = workload(args.time_samples, args.subset)
-    per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     nthr = host_cores()
-    # the sample is sized for about per_step seconds of all-cores work
-    smp = oracle_sample(ob, kw, per_step * nthr)
+    # the same fixed sample as the cpu_baseline leg of the GPU arm
+    smp = oracle_sample(ob, kw)
     for _ in range(args.warmup):
         oracle_step_parallel(smp, nthr)
     ts = [oracle_step_parallel(smp, nthr) for _ in range(args.steps)]
@@ -253,7 +263,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(ob, kw, None),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": nthr, "kind": "oracle",
-                             "sample": sample_text(smp, nthr)},
+                             "sample": sample_text(smp, nthr),
+                             "value_sample_unscaled": oracle_mvis_unscaled(smp, t)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -269,6 +280,98 @@ def workload_config(ob, kw, info):
         cfg.update({"nvalid": int(info.nvalid), "mean_taps": round(info.mean_taps, 1),
                     "tile": info.tile, "chunk": info.chunk})
     return cfg
+
+
+# ----------------------------------------------------------------------------- configurations 2 and 4
+def wproj_section(ctx, dev, args, stream):
+    """Configuration 2 (Stokes-I w-projection: 20.16M visibilities, 2048^2,
+    32 w planes, supports 8-64, OS 8) and configuration 4 (the same inputs
+    with BF16 / FP16 kernel tables, FP32 products and accumulation): per
+    storage, grid + degrid Mvis/s with the fastest gridding schedule of a
+    few candidates timed on the full data, the roofline of each step, and
+    the dirty image of each 16-bit form against the FP32 one (peak-relative
+    max and RMS error, dynamic range)."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import synthetic as sy
+    ob = sy.observation(2)
+    kw = sy.config_spec(2, ob)
+    N = kw["N"]
+    vd, keep = aw.device_observation(ob, dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    vis = torch.randn((ob.nvis, 1), dtype=torch.complex64, device=dev, generator=gen)
+    model = torch.randn((1, N, N), dtype=torch.complex64, device=dev, generator=gen)
+    out = torch.empty_like(vis)
+    grid = torch.zeros((1, N, N), dtype=torch.complex64, device=dev)
+    peak, _ = fp32_peak_tflops(dev.index or 0)
+    cands = {"tiles": aw.aw_tune(32, 256, 4, 1024, aw.AW_GRID_TILES, 0),
+             "offsets": aw.aw_tune(32, 256, 4, 256, aw.AW_GRID_OFFSETS, 0),
+             "hybrid/16": aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_HYBRID, 16),
+             "hybrid/24": aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_HYBRID, 24)}
+
+    def ms_of(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res, images = {}, {}
+    for name, stg in (("fp32", aw.AW_STORAGE_FP32), ("bf16", aw.AW_STORAGE_BF16), ("fp16", aw.AW_STORAGE_FP16)):
+        kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID, storage=stg)
+        kd = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID, storage=stg)
+        grid_ms, plans = {}, {}
+        for cname, t in cands.items():
+            plans[cname] = aw.aw_plan_create(ctx, vd, kg, tune=t)
+            p_ = plans[cname]
+
+            def g_():
+                grid.zero_()
+                aw.aw_grid_batched(ctx, p_, kg, vis, None, grid)
+            grid_ms[cname] = ms_of(g_)
+        best = min(grid_ms, key=grid_ms.get)
+        plan = plans[best]
+        info = aw.aw_plan_query(plan)
+        d_ms = ms_of(lambda: aw.aw_degrid(ctx, plan, kd, model, out))
+        st = None
+        grid.zero_()
+        st = aw.aw_grid_batched(ctx, plan, kg, vis, None, grid, want_stats=True)
+        img = torch.empty((1, N, N), dtype=torch.float32, device=dev)
+        aw.aw_fft_to_image(ctx, kg, grid.clone(), st.weight_sum, img)
+        images[name] = img
+        flops = 8.0 * info.mean_taps * info.nvalid     # one complex MAC (8 flop) per tap
+        g_ms = grid_ms[best]
+        res[name] = {"mvis_s": ob.nvis / ((g_ms + d_ms) / 1e3) / 1e6, "grid_ms": g_ms, "degrid_ms": d_ms,
+                     "grid_schedule": best, "grid_ms_by_schedule": grid_ms,
+                     "roofline": {"grid": {"bound": "alu", "achieved": flops / (g_ms / 1e3) / 1e12, "peak": peak,
+                                           "unit": "TFLOP/s", "frac": flops / (g_ms / 1e3) / 1e12 / peak},
+                                  "degrid": {"bound": "alu", "achieved": flops / (d_ms / 1e3) / 1e12, "peak": peak,
+                                             "unit": "TFLOP/s", "frac": flops / (d_ms / 1e3) / 1e12 / peak}},
+                     "table_bytes": int(aw.aw_kernel_set_info(kg).bytes)}
+        del plans, plan, kg, kd
+        torch.cuda.empty_cache()
+    # configuration 4's image error: each 16-bit form against the FP32 path
+    # (the FP32 path itself is held to 1e-5 of the FP64 oracle by the tests),
+    # over the inner half of the Stokes I image
+    q = slice(N // 4, 3 * N // 4)
+    ref = images["fp32"][0, q, q]
+    pk = float(ref.abs().max())
+    for name in ("bf16", "fp16"):
+        d = images[name][0, q, q] - ref
+        res[name]["dirty_image_vs_fp32"] = {"max_rel_peak": float(d.abs().max()) / pk,
+                                            "rms_rel_peak": float(d.pow(2).mean().sqrt()) / pk}
+    info_all = {"workload": "configuration 2: Stokes-I w-projection, %d visibilities (2000 samples x 16 channels "
+                            "1.2-1.5 GHz), 2048^2, 32 w planes, supports 8-64, OS 8; configuration 4: the same "
+                            "inputs with BF16 / FP16 kernel tables" % ob.nvis,
+                "nvis": int(ob.nvis), "mean_taps": None}
+    return {**info_all, **res}
 
 
 # ----------------------------------------------------------------------------- learned surrogate
@@ -716,9 +819,64 @@ def learned_section(ctx, dev, args):
     gam = torch.empty((Nm, Nm), dtype=torch.float32, device=dev)
     ms_gamma = timed(lambda: aw.mosaic_gamma(ctx, B, 0.2, gam), reps=10)
     net_bytes = aw.aw_surrogate_nparams(sur) * 2
+    # configuration 5 in full: every visibility of the 7 hexagonal fields
+    # (10M each), each field gridded onto its own 2048^2 x 4 grid with its own
+    # exact tables, with the network inline (per-plane rejection against that
+    # field's tables, and every plane learned), and with the exact tables
+    full = None
+    if not args.no_learned_full:
+        del g_ref, plan_f
+        torch.cuda.empty_cache()
+        tot = {"nvis": 0, "exact_ms": 0.0, "learned_rejection_ms": 0.0, "learned_all_ms": 0.0,
+               "rejected_bins": 0, "nbins": 0}
+        per_field = []
+        for f in range(len(sy.mosaic_offsets())):
+            obf = sy.observation(5, field=f)
+            kwf = sy.config_spec(5, obf)
+            exf = aw.aw_make_kernels(ctx, **kwf)
+            vdf, holdf = aw.device_observation(obf, dev)
+            pf = aw.aw_plan_create(ctx, vdf, exf, tune=aw.aw_tune(64, 128, 2, 1024, aw.AW_GRID_REGION, 0))
+            genf = torch.Generator(device=dev)
+            genf.manual_seed(100 + f)
+            vf = torch.randn((obf.nvis, 4), dtype=torch.complex64, device=dev, generator=genf)
+            gf = torch.zeros((4, N, N), dtype=torch.complex64, device=dev)
+
+            def ex_():
+                gf.zero_()
+                aw.aw_grid_batched(ctx, pf, exf, vf, None, gf)
+
+            def le_():
+                gf.zero_()
+                aw.aw_grid_learned(ctx, pf, sur, exf, vf, None, gf)
+            t_ex = timed(ex_, reps=3)
+            tb, errf, nrejf = aw.aw_surrogate_tables(ctx, sur, exf, reject_rel=reject)
+            del tb
+            t_rej = timed(le_, reps=1)
+            tb, _, _ = aw.aw_surrogate_tables(ctx, sur, exf, reject_rel=1e9)
+            del tb
+            t_all = timed(le_, reps=1)
+            per_field.append({"field": f, "nvis": int(obf.nvis), "exact_ms": t_ex, "learned_rejection_ms": t_rej,
+                              "learned_all_ms": t_all, "rejected_bins": int(nrejf)})
+            tot["nvis"] += int(obf.nvis)
+            tot["exact_ms"] += t_ex
+            tot["learned_rejection_ms"] += t_rej
+            tot["learned_all_ms"] += t_all
+            tot["rejected_bins"] += int(nrejf)
+            tot["nbins"] += int(len(errf))
+            del exf, vdf, holdf, pf, vf, gf
+            torch.cuda.empty_cache()
+        full = {"workload": "configuration 5: 7 hexagonal fields 1 deg apart, every visibility (%d), each on "
+                            "its own 2048^2 x 4 grid with its own exact tables (1024 bins, supports 8-64, OS 8)"
+                            % tot["nvis"],
+                "mvis_s_exact_tables": tot["nvis"] / (tot["exact_ms"] / 1e3) / 1e6,
+                "mvis_s_learned_with_rejection": tot["nvis"] / (tot["learned_rejection_ms"] / 1e3) / 1e6,
+                "mvis_s_learned_inline_all_planes": tot["nvis"] / (tot["learned_all_ms"] / 1e3) / 1e6,
+                "rejected_bins": tot["rejected_bins"], "nbins": tot["nbins"], "per_field": per_field}
     degrid = None
     if not args.no_learned_degrid:
-        del g_ex, g_le, g_ref, fine, plan_f
+        del g_ex, g_le, fine
+        if full is None:
+            del g_ref, plan_f
         torch.cuda.empty_cache()
         degrid = learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, chi_c, chi_h)
     return {"workload": "mosaic field 0 of 7 (hexagonal, 1 deg), 2048^2 x 4, 1024 bins (32 w x 8 PA x 4 freq), "
@@ -730,6 +888,13 @@ def learned_section(ctx, dev, args):
             "grid_ms_exact": ms_ex,
             "inline_mlp_points": points, "inline_engine": "tcgen05 (FP16 operands, FP32 accumulators in TMEM)",
             "inline_mlp_tflops": mlp_flops / (ms_mlp / 1e3) / 1e12,
+            "inline_mlp_roofline": {"bound": "tensor", "achieved": mlp_flops / (ms_mlp / 1e3) / 1e12,
+                                    "peak": bf16_burst(), "unit": "TFLOP/s",
+                                    "frac": (mlp_flops / (ms_mlp / 1e3) / 1e12) / bf16_burst() if bf16_burst() else None,
+                                    "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json); dense FP16 "
+                                                   "has the same nominal tensor rate",
+                                    "note": "the inline step also runs layer 1 and the sines on the CUDA cores and "
+                                            "the gridding atomics"},
             "grid_ms_learned_inline_all_planes_mma_sync": ms_mlp_sync,
             "inline_mlp_tflops_mma_sync": mlp_flops / (ms_mlp_sync / 1e3) / 1e12,
             "reference": "exact kernels at 128 w planes (4x finer); image errors over the inner half, Stokes I-V",
@@ -743,7 +908,7 @@ def learned_section(ctx, dev, args):
             "reject_threshold": reject, "rejected_bins": int(nrej), "nbins": int(len(err)),
             "network_bytes_fp16": int(net_bytes), "exact_table_bytes": int(aw.aw_kernel_set_info(exact).bytes),
             "exact_synthesis_s": t_synth, "surrogate_tables_s": t_tables,
-            "mosaic_gamma_ms_7x2048^2": ms_gamma, "degrid": degrid}
+            "mosaic_gamma_ms_7x2048^2": ms_gamma, "degrid": degrid, "mosaic_full": full}
 
 
 def learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, chi_c, chi_h):
@@ -1020,32 +1185,22 @@ def run_ours(args, rank, world, dist):
     dom = ("aw_grid (%s)" % gname) if g_ms >= d_ms else "aw_degrid (degrid_items_kernel)"
     peak_tflops, peak_src = fp32_peak_tflops(dev_index)
     achieved = flops / (dom_ms / 1e3) / 1e12
-    # DRAM bytes per launch of the dominant kernel, from the one-pass ncu capture summarised in
-    # profiles/dram_traffic_fullpol_aw_64M.md (same kernels, this workload, FP32 tables); null otherwise
-    # (the tile schedule depends on tile and chunk, the offset-grouped gridder on the super-tile and
-    # the CTAs in flight, the degridder on the super-tile)
-    measured_traffic = {("grid_persistent_kernel", 63851035, 64, 128): 149.65e9,
-                        ("grid_offset_kernel", 63851035, 1024, 5): 44.46e9,
-                        ("hybrid", 63851035, 64, 128, 1024, 6, 2): 5.60e9 + 26.88e9,
-                        ("hybrid", 63851035, 64, 128, 1024, 7, 2): 6.44e9 + 24.96e9,
-                        ("hybrid", 63851035, 64, 128, 1024, 8, 2): 7.20e9 + 24.75e9,
-                        ("degrid_items_kernel", 63851035, 1024): 13.96e9}
-    kname = gname if g_ms >= d_ms else "degrid_items_kernel"
-    if tune.grid_mode == aw.AW_GRID_HYBRID and g_ms >= d_ms:
-        # the two parts of one gridding step (tile kernel on the low w planes, offset kernel on
-        # the rest): their DRAM bytes added
-        dom_kernel = ("hybrid", int(nvis), tune.tile, tune.chunk, tune.dg_tile or 1024, tune.split_planes,
-                      tune.ctas_per_sm)
-    elif kname == "grid_persistent_kernel":
-        dom_kernel = (kname, int(nvis), tune.tile, tune.chunk)
-    elif kname == "grid_offset_kernel":
-        dom_kernel = (kname, int(nvis), tune.dg_tile or 1024, tune.ctas_per_sm)
-    else:
-        dom_kernel = (kname, int(nvis), tune.dg_tile or 1024)
-    traffic = measured_traffic.get(dom_kernel) if not args.subset else None
+    # DRAM bytes per launch of the dominant kernel: the one-bin-pair ncu capture summarised in
+    # profiles/dram_traffic_fullpol_aw_1pair.md (1,139,896 visibilities: region gridding 146.6 MB,
+    # degridding 96.7 MB), scaled to this workload by the visibility count (the per-visibility bytes
+    # scale; the tables touched per visibility grow with the bins, so this is a lower bound).  Only
+    # for the region schedule and the degridder at full size; null otherwise.
+    per_vis = {"region": 146.6e6 / 1139896, "degrid_items_kernel": 96.7e6 / 1139896}
+    traffic = None
+    if not args.subset:
+        if g_ms >= d_ms and tune.grid_mode == aw.AW_GRID_REGION:
+            traffic = per_vis["region"] * info.nvalid
+        elif g_ms < d_ms:
+            traffic = per_vis["degrid_items_kernel"] * info.nvalid
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": traffic,
-            "traffic_source": "profiles/dram_traffic_fullpol_aw_64M.md" if traffic else None,
+            "traffic_source": ("profiles/dram_traffic_fullpol_aw_1pair.md, scaled by the visibility count "
+                               "(lower bound)") if traffic else None,
             "peak_source": peak_src, "flops_per_launch": flops}
     alt = bf16_scaled_peak()
     if alt:
@@ -1179,20 +1334,28 @@ def run_ours(args, rank, world, dist):
     if not args.no_baselines and not args.subset:
         baselines = baselines_section(ctx, dev, ob, kw, tune, vis, model, grid, vis_out, stream, variants["fp32"])
     learned = None
-    if not args.no_learned:
-        # free the FP32 workload before the learned comparison
+    if not args.no_learned or not args.no_wproj:
+        # free the FP32 workload before the other configurations
         del vis, vis_out, model, kd
         torch.cuda.empty_cache()
+    wproj = None
+    if not args.no_wproj and not args.subset:
+        wproj = wproj_section(ctx, dev, args, stream)
+        torch.cuda.empty_cache()
+    if not args.no_learned:
         learned = learned_section(ctx, dev, args)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        smp = oracle_sample(ob, kw, args.cpu_seconds)
+        smp = oracle_sample(ob, kw)
         t1 = oracle_step(smp)
         nthr = host_cores()
-        tp = oracle_step_parallel(smp, nthr)
+        oracle_step_parallel(smp, nthr)   # warm-up (shards, threads)
+        tp = statistics.median([oracle_step_parallel(smp, nthr) for _ in range(3)])
         cpu = {"value": oracle_mvis(smp, tp), "unit": UNIT, "cores": nthr, "kind": "oracle",
                "sample": sample_text(smp, nthr), "seconds": tp,
-               "one_thread": {"value": oracle_mvis(smp, t1), "seconds": t1}}
+               "value_sample_unscaled": oracle_mvis_unscaled(smp, tp),
+               "one_thread": {"value": oracle_mvis(smp, t1), "seconds": t1,
+                              "value_sample_unscaled": oracle_mvis_unscaled(smp, t1)}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1213,7 +1376,8 @@ def run_ours(args, rank, world, dist):
                          "dg_tile": tune.dg_tile or 1024, "degrid_items": info.nitems_degrid,
                          "grid_schedule": SCHEDULES[tune.grid_mode], "split_planes": tune.split_planes,
                          "confirmed": confirm},
-                "clean": clean, "mosaic": mosaic, "per_baseline_kernels": baselines, "learned": learned}
+                "clean": clean, "mosaic": mosaic, "per_baseline_kernels": baselines, "learned": learned,
+                "wproj_stokes_i": wproj}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -1265,6 +1429,14 @@ def fp32_peak_tflops(device_index: int = 0):
         mhz, src = 2070.0, "nominal maximum SM clock"
     return (sms * 128 * 2 * mhz * 1e6 / 1e12,
             "FP32 CUDA-core peak derived: %d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz (%s)" % (sms, mhz, src))
+
+
+def bf16_burst():
+    """The measured dense bf16 tensor burst (TFLOP/s), or None."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return None
 
 
 def bf16_scaled_peak():
