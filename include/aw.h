@@ -513,6 +513,20 @@ enum { AW_ENGINE_MMA_SYNC = 0, AW_ENGINE_TCGEN05 = 1 };
 int aw_surrogate_set_engine(aw_surrogate *sur, int32_t engine);
 
 /*
+ * aw_surrogate_set_train_engine - where the products of a training step (and
+ * of aw_surrogate_loss_grad) run.  AW_TRAIN_TCGEN05 (default): for a network
+ * of width 128 with at least 2 hidden layers, every layer but the first as
+ * tcgen05.mma (FP16 operands: activations, weights, output errors; FP32
+ * accumulation, FP32 master weights and Adam), the weight gradients as
+ * GEMMs over the batch; the batch must be a multiple of 128.  Other shapes
+ * fall back to AW_TRAIN_FP32.  AW_TRAIN_FP32: FP32 tiled GEMMs on the CUDA
+ * cores.  The network is Sec. 3.2's kernel synthesis stood in for by a
+ * coordinate MLP (see aw_surrogate_create).  AW_EINVAL for another value.
+ */
+enum { AW_TRAIN_FP32 = 0, AW_TRAIN_TCGEN05 = 1 };
+int aw_surrogate_set_train_engine(aw_surrogate *sur, int32_t engine);
+
+/*
  * aw_surrogate_set_freq_mode - the frequency the inline evaluation of
  * aw_grid_learned feeds the network.  AW_FREQ_BIN (default): the centre of
  * the visibility's beam-frequency bin, as the exact tables average the beam

@@ -21,6 +21,7 @@ AW_STORAGE_FP32, AW_STORAGE_BF16, AW_STORAGE_FP16 = 0, 1, 2
 AW_GRID_TILES, AW_GRID_OFFSETS, AW_GRID_HYBRID, AW_GRID_REGION = 0, 1, 2, 3
 AW_INTERP_BILINEAR, AW_INTERP_CUBIC = 0, 1
 AW_ENGINE_MMA_SYNC, AW_ENGINE_TCGEN05 = 0, 1
+AW_TRAIN_FP32, AW_TRAIN_TCGEN05 = 0, 1
 AW_FREQ_BIN, AW_FREQ_CHANNEL = 0, 1
 
 c_i32, c_i64, c_dbl, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -112,6 +113,7 @@ SIGNATURES = {
     "mosaic_gamma_noalloc": (ctypes.c_int, [c_p, c_i32, c_i32, ctypes.c_float, c_p, c_p]),
     "aw_image_to_grid": (ctypes.c_int, [c_p, c_p, c_p, c_p, c_p]),
     "aw_surrogate_set_engine": (ctypes.c_int, [c_p, c_i32]),
+    "aw_surrogate_set_train_engine": (ctypes.c_int, [c_p, c_i32]),
     "aw_surrogate_set_freq_mode": (ctypes.c_int, [c_p, c_i32]),
     "aw_debug_fail_alloc": (ctypes.c_int, [c_i64]),
     "aw_debug_alloc_stats": (ctypes.c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
@@ -598,6 +600,10 @@ def aw_surrogate_tables(ctx: Handle, sur: Handle, exact: Handle, reject_rel: flo
 
 def aw_surrogate_set_engine(sur: Handle, engine: int):
     _check(load().aw_surrogate_set_engine(sur.ptr, int(engine)), "aw_surrogate_set_engine")
+
+
+def aw_surrogate_set_train_engine(sur: Handle, engine: int):
+    _check(load().aw_surrogate_set_train_engine(sur.ptr, int(engine)), "aw_surrogate_set_train_engine")
 
 
 def aw_degrid_learned(ctx: Handle, plan: Handle, sur: Handle, fallback: Handle, model, vis_out, stream=None):

@@ -178,48 +178,89 @@ struct FeatureScales {
     float out_scale;
 };
 
-__device__ __forceinline__ void features_of(const SetView &v, const FeatureScales &fs, int bin, int fy, int fx,
-                                            int jy, int jx, float *x) {
+// The features of a bin that do not depend on the offset: x[2], x[3], x[4]
+// and the offset scale dsc (the half support of the normalisation plane of |w|).
+struct BinFeat {
+    double dsc;
+    float x2, x3, x4;
+};
+
+__device__ __forceinline__ BinFeat bin_features(const SetView &v, const FeatureScales &fs, int bin) {
     const int p = bin / (v.npa * v.nfb);
     const int a = (bin / v.nfb) % v.npa;
     const int f = bin % v.nfb;
-    const int S = v.bin_support[bin];
-    const int rho = (S - 2) * v.OS / 2;
-    const double du = (double)(jx * v.OS - rho - fx) / v.OS;
-    const double dv = (double)(jy * v.OS - rho - fy) / v.OS;
     const double w = v.nw > 1 ? (p + 0.5) * v.w_max / v.nw : 0.0;
     // offsets in units of the half support of the normalisation plane of |w|
     int pn = fs.w_max > 0 ? (int)floor(w * fs.norm_nw / fs.w_max) : 0;
     pn = min(max(pn, 0), fs.norm_nw - 1);
-    const double dsc = fs.D * (fs.norm[pn] / 2 + 1);
-    x[0] = (float)(du / dsc);
-    x[1] = (float)(dv / dsc);
-    x[2] = (float)(fs.w_max > 0 ? 2.0 * w / fs.w_max - 1.0 : -1.0);
-    x[3] = (float)((v.freq[f] - fs.f_c) / fs.f_h);
-    x[4] = (float)((v.pa[a] - fs.chi_c) / fs.chi_h);
+    BinFeat r;
+    r.dsc = fs.D * (fs.norm[pn] / 2 + 1);
+    r.x2 = (float)(fs.w_max > 0 ? 2.0 * w / fs.w_max - 1.0 : -1.0);
+    r.x3 = (float)((v.freq[f] - fs.f_c) / fs.f_h);
+    r.x4 = (float)((v.pa[a] - fs.chi_c) / fs.chi_h);
+    return r;
+}
+
+__device__ __forceinline__ void offset_features(const SetView &v, const BinFeat &bf, int S, int fy, int fx, int jy,
+                                                int jx, float *x) {
+    const int rho = (S - 2) * v.OS / 2;
+    const double du = (double)(jx * v.OS - rho - fx) / v.OS;
+    const double dv = (double)(jy * v.OS - rho - fy) / v.OS;
+    x[0] = (float)(du / bf.dsc);
+    x[1] = (float)(dv / bf.dsc);
+    x[2] = bf.x2;
+    x[3] = bf.x3;
+    x[4] = bf.x4;
+}
+
+__device__ __forceinline__ void features_of(const SetView &v, const FeatureScales &fs, int bin, int fy, int fx,
+                                            int jy, int jx, float *x) {
+    offset_features(v, bin_features(v, fs, bin), v.bin_support[bin], fy, fx, jy, jx, x);
+}
+
+// The per-bin features of every bin of a set.
+__global__ void bin_features_kernel(SetView v, FeatureScales fs, BinFeat *out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < v.nbins; b += gridDim.x * blockDim.x)
+        out[b] = bin_features(v, fs, b);
 }
 
 // Random training points from an exact kernel set: bins uniform, then fine
-// offset and tap uniform.
-__global__ void sample_kernel(SetView v, FeatureScales fs, uint64_t seed, int B, float *X, float *T) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-        const uint64_t r1 = splitmix64(seed ^ ((uint64_t)b * 0x2545F4914F6CDD1Dull));
-        const uint64_t r2 = splitmix64(r1);
-        const int bin = (int)(r1 % (uint64_t)v.nbins);
-        const int S = v.bin_support[bin];
-        const uint64_t L = (uint64_t)S * S;
-        const uint64_t pick = r2 % ((uint64_t)v.OS * v.OS * L);
-        const int tap = (int)(pick % L);
-        const int off = (int)(pick / L);
-        const int fy = off / v.OS, fx = off % v.OS;
-        const int jy = tap / S, jx = tap % S;
-        features_of(v, fs, bin, fy, fx, jy, jx, X + (int64_t)b * 5);
-        const int64_t base = v.bin_offset[bin] + (int64_t)off * L * v.P;
-        for (int m = 0; m < v.P; ++m) {
-            const float2 k = read_k(v.tab, v.storage, base + aw_tab_index(v.ce, L, tap, m));
-            T[(int64_t)b * 2 * v.P + 2 * m] = k.x * v.inv_scale / fs.out_scale;
-            T[(int64_t)b * 2 * v.P + 2 * m + 1] = k.y * v.inv_scale / fs.out_scale;
+// offset and tap uniform.  A block draws 256 points (one a thread: the draws
+// and the features), then gathers their targets together, thread q taking
+// element q mod P of point q div P, so that the table reads of one point sit
+// side by side and the targets leave as contiguous rows.
+__global__ void __launch_bounds__(256) sample_kernel(SetView v, FeatureScales fs, const BinFeat *bf, uint64_t seed,
+                                                     int B, float *X, float *T) {
+    __shared__ int64_t s_base[256], s_L[256];
+    __shared__ int s_tap[256];
+    for (int b0 = blockIdx.x * 256; b0 < B; b0 += gridDim.x * 256) {
+        const int b = b0 + threadIdx.x;
+        if (b < B) {
+            const uint64_t r1 = splitmix64(seed ^ ((uint64_t)b * 0x2545F4914F6CDD1Dull));
+            const uint64_t r2 = splitmix64(r1);
+            const int bin = (int)(r1 % (uint64_t)v.nbins);
+            const int S = v.bin_support[bin];
+            const uint64_t L = (uint64_t)S * S;
+            // pick < OS^2 S^2 <= 2^26 (OS <= 64, S <= 128): the rest in 32-bit arithmetic
+            const uint32_t pick = (uint32_t)(r2 % ((uint64_t)v.OS * v.OS * L));
+            const int tap = (int)(pick % (uint32_t)L);
+            const int off = (int)(pick / (uint32_t)L);
+            const int fy = off / v.OS, fx = off % v.OS;
+            const int jy = tap / S, jx = tap % S;
+            offset_features(v, bf[bin], S, fy, fx, jy, jx, X + (int64_t)b * 5);
+            s_base[threadIdx.x] = v.bin_offset[bin] + (int64_t)off * L * v.P;
+            s_L[threadIdx.x] = (int64_t)L;
+            s_tap[threadIdx.x] = tap;
         }
+        __syncthreads();
+        const int n = min(256, B - b0);
+        for (int q = threadIdx.x; q < n * v.P; q += blockDim.x) {
+            const int j = q / v.P, m = q - j * v.P;
+            const float2 k = read_k(v.tab, v.storage, s_base[j] + aw_tab_index(v.ce, s_L[j], s_tap[j], m));
+            reinterpret_cast<float2 *>(T)[(int64_t)(b0 + j) * v.P + m] =
+                make_float2(k.x * v.inv_scale / fs.out_scale, k.y * v.inv_scale / fs.out_scale);
+        }
+        __syncthreads();
     }
 }
 
@@ -274,12 +315,6 @@ __global__ void store_points_kernel(SetView exact, FeatureScales fs, int bin, in
         atomicAdd(err2, e);
         atomicAdd(ref2, r);
     }
-}
-
-__global__ void copy_block_kernel(const void *src, void *dst, int64_t bytes) {
-    const int64_t n = bytes / 16;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
 }
 
 int nblk(int64_t n, int t = 256) {
@@ -415,9 +450,11 @@ static FeatureScales scales_of(const aw_surrogate *s) {
 
 struct DevBins {
     double *pa = nullptr, *freq = nullptr;
+    BinFeat *feat = nullptr;   // per-bin features (training)
     ~DevBins() {
         if (pa) aw_dev_free(pa);
         if (freq) aw_dev_free(freq);
+        if (feat) aw_dev_free(feat);
     }
 };
 
@@ -441,24 +478,37 @@ int aw_sur_train(aw_surrogate *s, const aw_kernel_set *k, const aw_train_cfg *tc
     if (rc) return rc;
     const SetView v = view_of(k, db.pa, db.freq);
     const FeatureScales fs = scales_of(s);
+    AW_CUDA_TRY(aw_dev_malloc(&db.feat, sizeof(BinFeat) * v.nbins));
+    BinFeat *d_bf = db.feat;
+    bin_features_kernel<<<nblk(v.nbins), 256, 0, st>>>(v, fs, d_bf);
+    AW_CHECK_LAUNCH();
     double *d_loss = nullptr;
     AW_CUDA_TRY(aw_dev_malloc(&d_loss, sizeof(double) * std::max(1, tc->steps)));
     AW_CUDA_TRY(cudaMemsetAsync(d_loss, 0, sizeof(double) * std::max(1, tc->steps), st));
+    // the tensor-core path (width 128) takes batches in multiples of 128 rows
+    const bool use_tc = aw_sur_use_tc(s) && B % 128 == 0;
+    if (use_tc) rc = aw_sur_tc_refresh(s, st);
     const auto t0 = std::chrono::steady_clock::now();
     for (int it = 0; it < tc->steps && rc == AW_OK; ++it) {
-        sample_kernel<<<nblk(B), 256, 0, st>>>(v, fs, tc->seed + 0x9E3779B97F4A7C15ull * (uint64_t)(it + 1), B, s->X,
-                                                s->T);
+        sample_kernel<<<nblk(B), 256, 0, st>>>(v, fs, d_bf, tc->seed + 0x9E3779B97F4A7C15ull * (uint64_t)(it + 1), B,
+                                                s->X, s->T);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { rc = aw_set_error(AW_ECUDA, "sample: %s", cudaGetErrorString(e)); break; }
-        rc = aw_sur_forward(s, s->X, B, st);
-        if (rc) break;
-        rc = aw_sur_backward(s, s->X, s->T, B, d_loss + it, st);
+        if (use_tc) {
+            rc = aw_sur_tc_step_grad(s, s->X, s->T, B, d_loss + it, st);
+        } else {
+            rc = aw_sur_forward(s, s->X, B, st);
+            if (rc) break;
+            rc = aw_sur_backward(s, s->X, s->T, B, d_loss + it, st);
+        }
         if (rc) break;
         // cosine decay from lr to lr_final
         const double fr = tc->steps > 1 ? (double)it / (tc->steps - 1) : 1.0;
         const float lr = (float)(tc->lr_final + 0.5 * (tc->lr - tc->lr_final) * (1.0 + std::cos(M_PI * fr)));
         rc = aw_sur_adam(s, lr, st);
+        if (rc == AW_OK && use_tc) rc = aw_sur_tc_refresh(s, st);
     }
+    if (rc == AW_OK && use_tc) rc = aw_sur_tc_check(s, st);
     std::vector<double> losses(std::max(1, tc->steps));
     if (rc == AW_OK) {
         cudaError_t e = cudaMemcpyAsync(losses.data(), d_loss, sizeof(double) * losses.size(), cudaMemcpyDeviceToHost, st);
@@ -619,6 +669,7 @@ int aw_sur_init(aw_surrogate *s) {
 }
 
 void aw_sur_free(aw_surrogate *s) {
+    aw_sur_tc_free(s);
     for (float *p : s->work) aw_dev_free(p);
     if (s->d_rejected) aw_dev_free(s->d_rejected);
     if (s->d_err) aw_dev_free(s->d_err);

@@ -32,7 +32,21 @@ struct aw_surrogate {
     unsigned int *d_err = nullptr;
     // frequency fed to the inline evaluation (AW_FREQ_*)
     int freq_mode = AW_FREQ_BIN;
+    // training engine (AW_TRAIN_*) and the tensor-core path's work buffers
+    int train_engine = AW_TRAIN_TCGEN05;
+    struct aw_sur_tc *tc = nullptr;
 };
+
+// Tensor-core training (aw_mlp_tc.cu): width 128, at least 2 hidden layers.
+int aw_sur_tc_supported(const aw_surrogate *s);
+int aw_sur_tc_step_grad(aw_surrogate *s, const float *X, const float *T, int B, double *loss_dev, cudaStream_t st);
+int aw_sur_tc_refresh(aw_surrogate *s, cudaStream_t st);
+int aw_sur_tc_check(aw_surrogate *s, cudaStream_t st);
+void aw_sur_tc_free(aw_surrogate *s);
+// whether training and loss_grad take the tensor-core path
+inline bool aw_sur_use_tc(const aw_surrogate *s) {
+    return s->train_engine == AW_TRAIN_TCGEN05 && aw_sur_tc_supported(s);
+}
 
 // Inline evaluation: gridding (model == NULL) or, with model and vis_out,
 // degridding (TCGEN05 engine only).

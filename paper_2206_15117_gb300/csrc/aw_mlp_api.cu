@@ -117,6 +117,13 @@ int aw_surrogate_forward(aw_ctx *ctx, aw_surrogate *s, const float *X, int32_t B
     SUR_GUARD_END
 }
 
+int aw_surrogate_set_train_engine(aw_surrogate *s, int32_t engine) {
+    if (!s) return aw_set_error(AW_EINVAL, "surrogate is NULL");
+    if (engine != AW_TRAIN_FP32 && engine != AW_TRAIN_TCGEN05) return aw_set_error(AW_EINVAL, "engine %d", engine);
+    s->train_engine = engine;
+    return AW_OK;
+}
+
 int aw_surrogate_loss_grad(aw_ctx *ctx, aw_surrogate *s, const float *X, const float *T, int32_t B, double *loss,
                            float *grad, void *stream) {
     SUR_GUARD_BEGIN
@@ -129,8 +136,14 @@ int aw_surrogate_loss_grad(aw_ctx *ctx, aw_surrogate *s, const float *X, const f
     double *d_loss = nullptr;
     AW_CUDA_TRY(aw_dev_malloc(&d_loss, sizeof(double)));
     cudaMemsetAsync(d_loss, 0, sizeof(double), st);
-    rc = aw_sur_forward(s, X, B, st);
-    if (rc == AW_OK) rc = aw_sur_backward(s, X, T, B, d_loss, st);
+    if (aw_sur_use_tc(s) && B % 128 == 0) {
+        rc = aw_sur_tc_refresh(s, st);
+        if (rc == AW_OK) rc = aw_sur_tc_step_grad(s, X, T, B, d_loss, st);
+        if (rc == AW_OK) rc = aw_sur_tc_check(s, st);
+    } else {
+        rc = aw_sur_forward(s, X, B, st);
+        if (rc == AW_OK) rc = aw_sur_backward(s, X, T, B, d_loss, st);
+    }
     if (rc == AW_OK) {
         cudaError_t e = cudaMemcpyAsync(grad, s->d_g, sizeof(float) * s->nparam, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, st);
