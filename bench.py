@@ -59,6 +59,8 @@ def parse():
                     help="skip the full configuration-5 mosaic (7 fields x 10M visibilities)")
     ap.add_argument("--learned-inline-case", type=int, default=None, metavar="ENGINE",
                     help="only run the small inline-surrogate profiling case on engine 0 (mma.sync) or 1 (tcgen05)")
+    ap.add_argument("--learned-train-case", type=int, default=None, metavar="STEPS",
+                    help="only run the small surrogate-training profiling case for STEPS steps")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
     ap.add_argument("--no-mosaic", action="store_true", help="skip the mosaic measurements")
     ap.add_argument("--no-baselines", action="store_true", help="skip the per-baseline kernel measurement")
@@ -347,6 +349,7 @@ def wproj_section(ctx, dev, args, stream):
         aw.aw_fft_to_image(ctx, kg, grid.clone(), st.weight_sum, img)
         images[name] = img
         flops = 8.0 * info.mean_taps * info.nvalid     # one complex MAC (8 flop) per tap
+        mean_taps = float(info.mean_taps)
         g_ms = grid_ms[best]
         res[name] = {"mvis_s": ob.nvis / ((g_ms + d_ms) / 1e3) / 1e6, "grid_ms": g_ms, "degrid_ms": d_ms,
                      "grid_schedule": best, "grid_ms_by_schedule": grid_ms,
@@ -370,7 +373,7 @@ def wproj_section(ctx, dev, args, stream):
     info_all = {"workload": "configuration 2: Stokes-I w-projection, %d visibilities (2000 samples x 16 channels "
                             "1.2-1.5 GHz), 2048^2, 32 w planes, supports 8-64, OS 8; configuration 4: the same "
                             "inputs with BF16 / FP16 kernel tables" % ob.nvis,
-                "nvis": int(ob.nvis), "mean_taps": None}
+                "nvis": int(ob.nvis), "mean_taps": mean_taps}
     return {**info_all, **res}
 
 
@@ -902,7 +905,8 @@ def learned_section(ctx, dev, args):
             "dirty_image_rel_err_learned_with_rejection_vs_ref": img_err, "dynamic_range_learned_with_rejection": dr,
             "dirty_image_rel_err_learned_all_planes_vs_ref": mlp_err, "dynamic_range_learned_all_planes": mlp_dr,
             "train": {"steps": rep.steps, "batch": 65536, "seconds": rep.seconds, "loss_first": rep.loss_first,
-                      "loss_last": rep.loss_last, "set": "exact kernels at 128 w planes x 8 PA x 4 freq"},
+                      "loss_last": rep.loss_last, "set": "exact kernels at 128 w planes x 8 PA x 4 freq",
+                      "engine": "tcgen05 kind::f16 (FP16 operands, FP32 accumulators and master weights)"},
             "kernel_rel_l2_per_w_plane": [round(e, 4) for e in plane_err],
             "kernel_rel_l2_per_w_plane_held_out_os7": [round(e, 4) for e in plane_err_held],
             "reject_threshold": reject, "rejected_bins": int(nrej), "nbins": int(len(err)),
@@ -976,6 +980,28 @@ def learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, ch
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def learned_train_case(steps: int):
+    """A small case for profiling surrogate training on the tensor cores: an exact full-pol set of
+    512^2 x 4, 4 w planes (supports 8, 8, 12, 16), OS 8, one PA and frequency bin; a 5 -> 128 x 4 -> 32
+    network trained for `steps` steps on batches of 65,536 points (the configuration-5 batch), so that
+    each layer's activations (16.8 MB in FP16) exceed neither the device nor an ncu capture's budget."""
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import build as awbuild
+    awbuild.build()
+    ctx = aw.aw_create(0)
+    N = 512
+    kw = dict(N=N, dl=math.radians(2.0) / N, OS=8, W=7.0, npol=4, nw=4, w_max=2000.0, supports=[8, 8, 12, 16])
+    exact = aw.aw_make_kernels(ctx, **kw)
+    sur = aw.aw_surrogate_create(ctx, npol=4, width=128, n_hidden=4, omega0=30.0, D=1.0,
+                                 norm_supports=kw["supports"], w_max=kw["w_max"], f_c=1.4e9, f_h=0.2e9, chi_c=0.0,
+                                 chi_h=1.5, out_scale=1.0, seed=11)
+    rep = aw.aw_surrogate_train(ctx, sur, exact, steps=steps, batch=65536, lr=1e-3, lr_final=1e-5, seed=3)
+    print(json.dumps({"case": "learned_train", "engine": "tcgen05", "steps": rep.steps, "batch": 65536,
+                      "seconds": rep.seconds, "ms_per_step": rep.seconds * 1e3 / max(1, rep.steps),
+                      "loss_first": rep.loss_first, "loss_last": rep.loss_last}))
+    return 0
+
+
 def learned_inline_case(engine: int):
     """A small case for profiling the inline surrogate: the full-pol test geometry (256^2 x 4,
     3 w planes x 2 PA x 2 frequency bins, supports 16-24, OS 8), 57,600 visibilities, a randomly
@@ -1212,8 +1238,15 @@ def run_ours(args, rank, world, dist):
     # with the faster of the two schedules on its own tables, as aw_autotune on that kernel set would
     # choose (halving the table bytes moves the tile schedule's L2 stream, not the atomics)
     schedules = SCHEDULES
+
+    def var_roof(gm_, dm_):
+        # every table precision computes in FP32: the same FP32 peak for all three
+        return {k_: {"bound": "alu", "achieved": flops / (t_ / 1e3) / 1e12, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": flops / (t_ / 1e3) / 1e12 / peak_tflops}
+                for k_, t_ in (("grid", gm_), ("degrid", dm_))}
+
     variants = {"fp32": {"grid_ms": g_ms, "degrid_ms": d_ms, "mvis_s": nvis / ((g_ms + d_ms) / 1e3) / 1e6,
-                         "grid_schedule": schedules[tune.grid_mode]}}
+                         "grid_schedule": schedules[tune.grid_mode], "roofline": var_roof(g_ms, d_ms)}}
     if not args.no_variants:
         for name, stg in (("bf16", aw.AW_STORAGE_BF16), ("fp16", aw.AW_STORAGE_FP16)):
             kg2 = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID, storage=stg)
@@ -1231,7 +1264,7 @@ def run_ours(args, rank, world, dist):
             gm, dm = res[best]
             variants[name] = {"grid_ms": gm, "degrid_ms": dm, "mvis_s": nvis / ((gm + dm) / 1e3) / 1e6,
                               "grid_schedule": best, "grid_ms_by_schedule": {k_: v_[0] for k_, v_ in res.items()},
-                              "table_bytes": int(aw.aw_kernel_set_info(kg2).bytes)}
+                              "table_bytes": int(aw.aw_kernel_set_info(kg2).bytes), "roofline": var_roof(gm, dm)}
             del kg2, kd2
             torch.cuda.empty_cache()
     alt_plans = []
@@ -1452,6 +1485,8 @@ def main():
     args = parse()
     if args.learned_inline_case is not None:
         return learned_inline_case(args.learned_inline_case)
+    if args.learned_train_case is not None:
+        return learned_train_case(args.learned_train_case)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
