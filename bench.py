@@ -310,7 +310,12 @@ def wproj_section(ctx, dev, args, stream):
     cands = {"tiles": aw.aw_tune(32, 256, 4, 1024, aw.AW_GRID_TILES, 0),
              "offsets": aw.aw_tune(32, 256, 4, 256, aw.AW_GRID_OFFSETS, 0),
              "hybrid/16": aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_HYBRID, 16),
-             "hybrid/24": aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_HYBRID, 24)}
+             "hybrid/24": aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_HYBRID, 24),
+             # the region kernel for supports 16-48 (8 and wider on OFFSETS beside it)
+             "region": aw.aw_tune(32, 256, 2, 1024, aw.AW_GRID_REGION, 0),
+             "region/14": aw.aw_tune(32, 256, 2, 1024, aw.AW_GRID_REGION, 14),
+             "region/18": aw.aw_tune(32, 256, 2, 1024, aw.AW_GRID_REGION, 18),
+             "region/22": aw.aw_tune(32, 256, 2, 1024, aw.AW_GRID_REGION, 22)}
 
     def ms_of(fn, reps=5):
         fn()

@@ -168,15 +168,17 @@ typedef struct aw_tune {
  * the call forks from and joins back into the caller's stream, also inside
  * the graph of aw_grid_batched).  The TILES kernel is bound by the L2->SM
  * stream of kernel values, the OFFSETS kernel by its atomics, so sharing the
- * SMs between them beats either alone.  REGION (full polarisation): work
- * items of one bin and one grid tile whose side is chosen per support, sorted
- * by oversampled offset; the CTA accumulates the tile's output region (tile +
- * support - 1 cells square, at most 56) in shared memory, each thread holding
- * one kernel tap's Mueller values in registers for all visibilities of an
- * offset, and adds the region to the grid once; bins whose support does not
- * fit (above 49 cells) take OFFSETS on the plan's second stream at the same
- * time.  Stokes-I plans given REGION grid every bin with OFFSETS.  All modes
- * give the same grid up to FP32 rounding order. */
+ * SMs between them beats either alone.  REGION: work items of one bin and
+ * one grid tile whose side is chosen per support, sorted by oversampled
+ * offset; the CTA accumulates the tile's output region (tile + support - 1
+ * cells square, at most 56) in shared memory, each thread holding kernel
+ * taps in registers for all visibilities of an offset (full-pol: one tap's 16
+ * Mueller values; Stokes I: up to 18 taps of one value), and adds the region to
+ * the grid once; bins of planes from split_planes on, and bins whose support
+ * has no region form (above 49 cells; full-pol: rows that do not split into
+ * passes of 32 taps over 4-10 warps; Stokes I: not a multiple of 4), take
+ * OFFSETS on the plan's second stream at the same time.  All modes give the
+ * same grid up to FP32 rounding order. */
 enum { AW_GRID_TILES = 0, AW_GRID_OFFSETS = 1, AW_GRID_HYBRID = 2, AW_GRID_REGION = 3 };
 
 typedef struct aw_plan_info {

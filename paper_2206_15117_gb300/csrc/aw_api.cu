@@ -357,7 +357,7 @@ static int launch_planned(aw_ctx *ctx, const aw_plan *p, const aw_kernel_set *k,
         // kernel on the second stream at the same time, one CTA per SM (it
         // fits beside two region CTAs: registers, shared memory, threads)
         if (p->nitems_ho == 0) return aw_launch_grid_region(p, k, vis, weight, grid, s);
-        if (p->nreg == 0) {   // no bin takes a region (e.g. Stokes I): OFFSETS alone, every SM
+        if (p->nreg == 0) {   // no bin takes a region: OFFSETS alone, every SM
             aw_grid_launch Lo{p, k, vis, weight, grid, false, 0, s, AW_GRID_OFFSETS, p->d_items_ho, p->nitems_ho};
             return aw_launch_grid(Lo);
         }
@@ -549,10 +549,11 @@ int aw_autotune(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *k, aw_
         if (rc) break;
         if (ms_best < best) { best = ms_best; bt = tu; }
     }
-    // the region schedule (full polarisation): the w planes up to the last one
-    // whose support is at most 32, 40 or 48 cells on the region kernel, the rest
-    // on OFFSETS at the same time (its super-tile the larger one)
-    if (!rc && k->spec.npol == 4) {
+    // the region schedule: the w planes up to the last one whose support is at
+    // most 32, 40 or 48 cells on the region kernel (bins whose support has no
+    // region form stay on OFFSETS), the rest on OFFSETS at the same time (its
+    // super-tile the larger one)
+    if (!rc) {
         int last_split = -1;
         for (int lim : {32, 40, 48}) {
             int q = 0;

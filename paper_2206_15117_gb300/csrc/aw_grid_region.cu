@@ -59,6 +59,7 @@ __device__ __forceinline__ bool rg_bounds_ok(bool ok, unsigned int code) {
 enum : unsigned int { BC_R_REC = 14, BC_R_CELL, BC_R_TAB, BC_R_GRID, BC_R_SMEM };
 
 constexpr int RG_CH = 128;      // visibilities staged per round
+constexpr int RG_TPL1 = 18;     // most taps a lane in the Stokes-I form ((48 / 4) 48 / 32)
 constexpr int RG_MAXT = 320;    // largest CTA (10 warps)
 // resident CTAs per SM the register budget is set for (the region size,
 // AW_RG_RMAX, decides the shared-memory side), and whether the next unit's
@@ -129,6 +130,18 @@ struct RgK<AW_STORAGE_BF16> : RgK16<AW_STORAGE_BF16> {};
 template <>
 struct RgK<AW_STORAGE_FP16> : RgK16<AW_STORAGE_FP16> {};
 
+// Stokes I (one value per tap, one per table element): tap t at idx + t
+template <int ST>
+__device__ __forceinline__ float2 rg_k1(const void *base, int64_t idx, int t) {
+    if constexpr (ST == AW_STORAGE_FP32) {
+        return __ldg(reinterpret_cast<const float2 *>(base) + idx + t);
+    } else {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t *>(base) + idx + t);
+        if constexpr (ST == AW_STORAGE_BF16) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+        else return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    }
+}
+
 __device__ __forceinline__ void cmac2(float &re, float &im, float2 k, float vr, float vi) {
     re = fmaf(k.x, vr, re);
     re = fmaf(-k.y, vi, re);
@@ -136,15 +149,62 @@ __device__ __forceinline__ void cmac2(float &re, float &im, float2 k, float vr, 
     im = fmaf(k.y, vr, im);
 }
 
-template <int ST, int R>
-__global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(RegionArgs a) {
-    constexpr int NPOL = 4, P = 16, RR = R * R;
+// Shared memory of one CTA: the region (R^2 cells of NPOL complex FP32
+// accumulators), the staged visibilities (NPOL complex each) and four int
+// arrays of the round.
+constexpr size_t region_smem_bytes(int R, int npol) {
+    return (size_t)R * R * npol * 8 + (size_t)RG_CH * npol * 8 + (size_t)RG_CH * 2 * sizeof(int) +
+           (size_t)(RG_CH + 1) * 2 * sizeof(int);
+}
+
+// One full-polarisation visibility-tap: the region cell (planes (0, 1) in c01,
+// (2, 3) in c23) += K V, plane s getting the sum over correlations c of
+// K[s][c] V_c (the products formed while the cell is being read).
+__device__ __forceinline__ void mueller_update(float4 &c01, float4 &c23, const float2 (&k)[16], float4 v01,
+                                               float4 v23) {
+    float4 r01 = c01, r23 = c23;
+    cmac2(r01.x, r01.y, k[0], v01.x, v01.y);
+    cmac2(r01.z, r01.w, k[4], v01.x, v01.y);
+    cmac2(r23.x, r23.y, k[8], v01.x, v01.y);
+    cmac2(r23.z, r23.w, k[12], v01.x, v01.y);
+    cmac2(r01.x, r01.y, k[1], v01.z, v01.w);
+    cmac2(r01.z, r01.w, k[5], v01.z, v01.w);
+    cmac2(r23.x, r23.y, k[9], v01.z, v01.w);
+    cmac2(r23.z, r23.w, k[13], v01.z, v01.w);
+    cmac2(r01.x, r01.y, k[2], v23.x, v23.y);
+    cmac2(r01.z, r01.w, k[6], v23.x, v23.y);
+    cmac2(r23.x, r23.y, k[10], v23.x, v23.y);
+    cmac2(r23.z, r23.w, k[14], v23.x, v23.y);
+    cmac2(r01.x, r01.y, k[3], v23.z, v23.w);
+    cmac2(r01.z, r01.w, k[7], v23.z, v23.w);
+    cmac2(r23.x, r23.y, k[11], v23.z, v23.w);
+    cmac2(r23.z, r23.w, k[15], v23.z, v23.w);
+    c01 = r01;
+    c23 = r23;
+}
+
+// NPOL = 4: full polarisation, 16 Mueller values a tap, units of one offset
+// group and one pass of 32 taps a warp.  NPOL = 1: Stokes I, one value a tap
+// and one plane (an eighth of the shared memory); a single update per
+// visibility-tap leaves each read-modify-write little arithmetic to hide its
+// latency behind, so the CTA has only 4 warps (row classes), a lane takes
+// all its taps at once (a.passes of them, at most TMAX: taps lane, lane + 32,
+// ... of its warp's rows) and a unit is a whole offset group: a.passes
+// independent updates per visibility and lane.
+template <int ST, int R, int NPOL, int TMAX>
+__global__ void __launch_bounds__(NPOL == 4 ? RG_MAXT : 128, NPOL == 4 ? AW_RG_MINB : 4)
+    grid_region_kernel(RegionArgs a) {
+    constexpr int P = NPOL * NPOL, RR = R * R;
     extern __shared__ __align__(16) char rg_smem[];
     const int S = a.S, L = S * S, M = a.M, passes = a.passes;
+    // NPOL 4: planes (0, 1) and (2, 3) of a cell as two float4; NPOL 1: one float2
     float4 *reg01 = reinterpret_cast<float4 *>(rg_smem);
     float4 *reg23 = reg01 + RR;
-    float4 *s_v = reg23 + RR;                                   // [RG_CH][2]
-    int *s_cell = reinterpret_cast<int *>(s_v + 2 * RG_CH);     // [RG_CH] ly * R + lx
+    float2 *reg0 = reinterpret_cast<float2 *>(rg_smem);
+    char *after_region = rg_smem + (size_t)RR * NPOL * 8;
+    float4 *s_v = reinterpret_cast<float4 *>(after_region);     // NPOL 4: [RG_CH][2]
+    float2 *s_v1 = reinterpret_cast<float2 *>(after_region);    // NPOL 1: [RG_CH]
+    int *s_cell = reinterpret_cast<int *>(after_region + (size_t)RG_CH * NPOL * 8);   // [RG_CH] ly * R + lx
     int *s_key = s_cell + RG_CH;                                // [RG_CH] offset * 64 + ly mod M
     int *s_ss = s_key + RG_CH;                                  // [RG_CH + 1] sub-group starts
     int *s_gss = s_ss + RG_CH + 1;                              // [RG_CH + 1] first sub-group of each group
@@ -169,10 +229,17 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
         const int oy = (it.w >> 16) * a.T, ox = (it.w & 0xffff) * a.T;   // grid origin of the region
         const int64_t tab0 = a.bin_offset[bin];
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int c = tid; c < RR; c += BT) { reg01[c] = z4; reg23[c] = z4; }
+        if constexpr (NPOL == 4) {
+            for (int c = tid; c < RR; c += BT) { reg01[c] = z4; reg23[c] = z4; }
+        } else {
+            for (int c = tid; c < RR; c += BT) reg0[c] = make_float2(0.f, 0.f);
+        }
 
-        for (int c0 = 0; c0 < count; c0 += RG_CH) {
-            const int n = min(RG_CH, count - c0);
+        // a round stages one visibility a thread: at most RG_CH, and no more
+        // than the CTA's threads (the Stokes-I form runs 64-thread CTAs)
+        const int round = min(RG_CH, BT), nwr = round / 32;
+        for (int c0 = 0; c0 < count; c0 += round) {
+            const int n = min(round, count - c0);
             __syncthreads();   // the region is zeroed / the previous round's readers are done
             // ---- stage the round's visibilities (flipped, weighted, NaN-checked)
             if (tid < n) {
@@ -192,8 +259,10 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
                 if (r.flip) {
 #pragma unroll
                     for (int c = 0; c < NPOL; ++c) v[c].y = -v[c].y;
-                    float2 t = v[1]; v[1] = v[2]; v[2] = t;
-                    float tw = w[1]; w[1] = w[2]; w[2] = tw;
+                    if constexpr (NPOL == 4) {
+                        float2 t = v[1]; v[1] = v[2]; v[2] = t;
+                        float tw = w[1]; w[1] = w[2]; w[2] = tw;
+                    }
                 }
                 if (bad) {
                     nbad++;
@@ -208,8 +277,12 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
                     v[c] = make_float2(ws * v[c].x, ws * v[c].y);
                 }
                 wloc += wm / NPOL;
-                s_v[2 * tid] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-                s_v[2 * tid + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                if constexpr (NPOL == 4) {
+                    s_v[2 * tid] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+                    s_v[2 * tid + 1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                } else {
+                    s_v1[tid] = v[0];
+                }
                 const int ly = (int)r.y0 - oy, lx = (int)r.x0 - ox;
                 const bool inr = RG_BOK(ly >= 0 && lx >= 0 && ly + S <= R && lx + S <= R, BC_R_CELL);
                 s_cell[tid] = inr ? ly * R + lx : 0;
@@ -221,7 +294,7 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
             const bool fs = tid < n && (tid == 0 || s_key[tid] != s_key[tid - 1]);
             const bool fg = tid < n && (tid == 0 || (s_key[tid] >> 6) != (s_key[tid - 1] >> 6));
             const unsigned bs = __ballot_sync(0xffffffffu, fs), bg = __ballot_sync(0xffffffffu, fg);
-            if (lane == 0 && warp < RG_CH / 32) { s_wcs[warp] = __popc(bs); s_wcg[warp] = __popc(bg); }
+            if (lane == 0 && warp < nwr) { s_wcs[warp] = __popc(bs); s_wcg[warp] = __popc(bg); }
             __syncthreads();
             if (fs) {
                 int before_s = 0, before_g = 0;
@@ -233,7 +306,7 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
             }
             if (tid == 0) {
                 int ts = 0, tg = 0;
-                for (int w = 0; w < RG_CH / 32; ++w) { ts += s_wcs[w]; tg += s_wcg[w]; }
+                for (int w = 0; w < nwr; ++w) { ts += s_wcs[w]; tg += s_wcg[w]; }
                 s_ss[ts] = n;
                 s_gss[tg] = ts;
                 s_ng = tg;
@@ -256,8 +329,10 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
                 tap_of(u - g * passes, t, ct);
                 if (t >= 0) {
                     const int64_t kb = tab0 + (int64_t)(s_key[s_ss[s_gss[g]]] >> 6) * L * P;
-                    if (RG_BOK(kb >= 0 && kb + (int64_t)P * L <= a.tab_elems, BC_R_TAB))
-                        RgK<ST>::load(a.ktab, kb, L, t, k);
+                    if (RG_BOK(kb >= 0 && kb + (int64_t)P * L <= a.tab_elems, BC_R_TAB)) {
+                        if constexpr (NPOL == 4) RgK<ST>::load(a.ktab, kb, L, t, k);
+                        else k[0] = rg_k1<ST>(a.ktab, kb, t);
+                    }
                 }
             };
             auto run_unit = [&](int u, const float2 (&k)[P]) {
@@ -271,27 +346,14 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
                     for (int j = s_ss[sg]; j < j1; ++j) {
                         const int cell = s_cell[j] + ct;
                         if (act && RG_BOK(cell >= 0 && cell < RR, BC_R_SMEM)) {
-                            const float4 v01 = s_v[2 * j], v23 = s_v[2 * j + 1];
-                            float4 r01 = reg01[cell], r23 = reg23[cell];
-                            // plane s gets sum over correlations c of K[s][c] V_c
-                            cmac2(r01.x, r01.y, k[0], v01.x, v01.y);
-                            cmac2(r01.z, r01.w, k[4], v01.x, v01.y);
-                            cmac2(r23.x, r23.y, k[8], v01.x, v01.y);
-                            cmac2(r23.z, r23.w, k[12], v01.x, v01.y);
-                            cmac2(r01.x, r01.y, k[1], v01.z, v01.w);
-                            cmac2(r01.z, r01.w, k[5], v01.z, v01.w);
-                            cmac2(r23.x, r23.y, k[9], v01.z, v01.w);
-                            cmac2(r23.z, r23.w, k[13], v01.z, v01.w);
-                            cmac2(r01.x, r01.y, k[2], v23.x, v23.y);
-                            cmac2(r01.z, r01.w, k[6], v23.x, v23.y);
-                            cmac2(r23.x, r23.y, k[10], v23.x, v23.y);
-                            cmac2(r23.z, r23.w, k[14], v23.x, v23.y);
-                            cmac2(r01.x, r01.y, k[3], v23.z, v23.w);
-                            cmac2(r01.z, r01.w, k[7], v23.z, v23.w);
-                            cmac2(r23.x, r23.y, k[11], v23.z, v23.w);
-                            cmac2(r23.z, r23.w, k[15], v23.z, v23.w);
-                            reg01[cell] = r01;
-                            reg23[cell] = r23;
+                            if constexpr (NPOL == 1) {
+                                const float2 v = s_v1[j];
+                                float2 r = reg0[cell];
+                                cmac2(r.x, r.y, k[0], v.x, v.y);
+                                reg0[cell] = r;
+                            } else {
+                                mueller_update(reg01[cell], reg23[cell], k, s_v[2 * j], s_v[2 * j + 1]);
+                            }
                         }
                         // the next visibility's cells may be this one's cells of
                         // other lanes: its region reads come after these writes
@@ -302,34 +364,80 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
                     __syncthreads();
                 }
             };
-#if AW_RG_PREFETCH
-            float2 kA[P], kB[P];
+            if constexpr (NPOL == 1) {
+                const int tpl = passes;   // taps a lane: q = lane + 32 i, i < tpl, of (S / M) S
+                const int tw = (S / M) * S;
+                for (int g = 0; g < s_ng; ++g) {
+                    float2 k[TMAX];
+                    int ct[TMAX];
+                    const int64_t kb = tab0 + (int64_t)(s_key[s_ss[s_gss[g]]] >> 6) * L;
+                    const bool kok = RG_BOK(kb >= 0 && kb + (int64_t)L <= a.tab_elems, BC_R_TAB);
 #pragma unroll
-            for (int m = 0; m < P; ++m) { kA[m] = make_float2(0.f, 0.f); kB[m] = kA[m]; }
-            if (nunits > 0) load_unit(0, kA);
-            for (int u = 0; u < nunits; u += 2) {
-                if (u + 1 < nunits) load_unit(u + 1, kB);
-                run_unit(u, kA);
-                if (u + 1 < nunits) {
-                    if (u + 2 < nunits) load_unit(u + 2, kA);
-                    run_unit(u + 1, kB);
+                    for (int i = 0; i < TMAX; ++i) {
+                        const int q = lane + 32 * i;
+                        const int lr = q / S, tx = q - lr * S, ty = warp + lr * M;
+                        const bool on = i < tpl && q < tw && kok;
+                        ct[i] = on ? ty * R + tx : -1;
+                        k[i] = on ? rg_k1<ST>(a.ktab, kb, ty * S + tx) : make_float2(0.f, 0.f);
+                    }
+                    const int sg1 = s_gss[g + 1];
+                    for (int sg = s_gss[g]; sg < sg1; ++sg) {
+                        const int j1 = s_ss[sg + 1];
+                        for (int j = s_ss[sg]; j < j1; ++j) {
+                            const int base = s_cell[j];
+                            const float2 v = s_v1[j];
+#pragma unroll
+                            for (int i = 0; i < TMAX; ++i) {
+                                const int cell = base + ct[i];
+                                if (ct[i] >= 0 && RG_BOK(cell >= 0 && cell < RR, BC_R_SMEM)) {
+                                    float2 r = reg0[cell];
+                                    cmac2(r.x, r.y, k[i], v.x, v.y);
+                                    reg0[cell] = r;
+                                }
+                            }
+                            // the next visibility's cells may be this one's cells of other lanes
+                            __syncwarp();
+                        }
+                        // another footprint-row residue next: other warps may then write rows this warp wrote
+                        __syncthreads();
+                    }
                 }
-            }
-#else
-            for (int u = 0; u < nunits; ++u) {
-                float2 kA[P];
+            } else {
+#if AW_RG_PREFETCH
+                float2 kA[P], kB[P];
 #pragma unroll
-                for (int m = 0; m < P; ++m) kA[m] = make_float2(0.f, 0.f);
-                load_unit(u, kA);
-                run_unit(u, kA);
-            }
+                for (int m = 0; m < P; ++m) { kA[m] = make_float2(0.f, 0.f); kB[m] = kA[m]; }
+                if (nunits > 0) load_unit(0, kA);
+                for (int u = 0; u < nunits; u += 2) {
+                    if (u + 1 < nunits) load_unit(u + 1, kB);
+                    run_unit(u, kA);
+                    if (u + 1 < nunits) {
+                        if (u + 2 < nunits) load_unit(u + 2, kA);
+                        run_unit(u + 1, kB);
+                    }
+                }
+#else
+                for (int u = 0; u < nunits; ++u) {
+                    float2 kA[P];
+#pragma unroll
+                    for (int m = 0; m < P; ++m) kA[m] = make_float2(0.f, 0.f);
+                    load_unit(u, kA);
+                    run_unit(u, kA);
+                }
 #endif
+            }
         }
         __syncthreads();
         // ---- add the region to the grid (cells that received nothing are skipped)
         for (int c = tid; c < RR; c += BT) {
             const int cy = c / R, cx = c - cy * R;
             const int gy = oy + cy, gx = ox + cx;
+            if constexpr (NPOL == 1) {
+                const float2 v = reg0[c];
+                if ((v.x != 0.f || v.y != 0.f) && RG_BOK(gy < a.N && gx < a.N, BC_R_GRID))
+                    atomicAdd(a.grid + (int64_t)gy * a.N + gx, v);
+                continue;
+            }
             const float4 v01 = reg01[c], v23 = reg23[c];
             const bool nz = v01.x != 0.f || v01.y != 0.f || v01.z != 0.f || v01.w != 0.f ||
                             v23.x != 0.f || v23.y != 0.f || v23.z != 0.f || v23.w != 0.f;
@@ -358,17 +466,14 @@ __global__ void __launch_bounds__(RG_MAXT, AW_RG_MINB) grid_region_kernel(Region
     }
 }
 
-size_t region_smem_bytes(int R) {
-    return (size_t)2 * R * R * sizeof(float4) + (size_t)RG_CH * 2 * sizeof(float4) +
-           (size_t)RG_CH * 2 * sizeof(int) + (size_t)(RG_CH + 1) * 2 * sizeof(int);
-}
-
-template <int ST>
+template <int ST, int NPOL, int TMAX>
 int launch_region_t(const RegionArgs &a, int BT, int sm_count, cudaStream_t s) {
     static_assert(AW_RG_RMAX <= 64, "region side");
     if (a.R != AW_RG_RMAX) return aw_set_error(AW_EINVAL, "region side %d", a.R);
-    auto kern = grid_region_kernel<ST, AW_RG_RMAX>;
-    const size_t smem = region_smem_bytes(a.R);
+    if (NPOL == 1 && (a.passes > TMAX || (BT != 64 && BT != 128)))
+        return aw_set_error(AW_EINVAL, "Stokes-I region: %d taps a lane, %d threads", a.passes, BT);
+    auto kern = grid_region_kernel<ST, AW_RG_RMAX, NPOL, TMAX>;
+    const size_t smem = region_smem_bytes(a.R, NPOL);
     AW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 1;
     AW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem));
@@ -377,6 +482,13 @@ int launch_region_t(const RegionArgs &a, int BT, int sm_count, cudaStream_t s) {
     kern<<<(unsigned)blocks, BT, smem, s>>>(a);
     AW_CHECK_LAUNCH();
     return AW_OK;
+}
+
+template <int TMAX>
+int launch_region1(const RegionArgs &a, int st, int BT, int sm_count, cudaStream_t s) {
+    if (st == AW_STORAGE_FP32) return launch_region_t<AW_STORAGE_FP32, 1, TMAX>(a, BT, sm_count, s);
+    if (st == AW_STORAGE_BF16) return launch_region_t<AW_STORAGE_BF16, 1, TMAX>(a, BT, sm_count, s);
+    return launch_region_t<AW_STORAGE_FP16, 1, TMAX>(a, BT, sm_count, s);
 }
 
 }  // namespace
@@ -396,13 +508,19 @@ int aw_region_rows(int S) {
     return best_eff >= 0.74 ? best : 0;
 }
 
+// Stokes I: 4 warps (row classes) for supports that are multiples of 4 and
+// leave a lane at most RG_TPL1 taps; 0 if none.  (Measured on the 20.16M-
+// visibility Stokes-I w-projection set: 4 warps 7.9 ms, 2 warps with twice the
+// taps a lane 10.2 ms, 8-10 warps with one tap a lane 12.8 ms.)
+static int region1_rows(int S) { return S >= 8 && S % 4 == 0 && ((S / 4) * S + 31) / 32 <= RG_TPL1 ? 4 : 0; }
+
 int aw_region_tile(int S, int npol) {
-    if (npol != 4 || S < 2 || aw_region_rows(S) == 0) return 0;
+    if (npol == 4 ? (S < 2 || aw_region_rows(S) == 0) : (npol != 1 || region1_rows(S) == 0)) return 0;
     const int T = AW_RG_RMAX - S + 1;
     return T >= 8 ? T : 0;
 }
 
-int aw_region_threads(int S) { return 32 * aw_region_rows(S); }
+int aw_region_threads(int S, int npol) { return 32 * (npol == 1 ? region1_rows(S) : aw_region_rows(S)); }
 
 int aw_launch_grid_region(const aw_plan *p, const aw_kernel_set *k, const void *vis, const float *weight, void *grid,
                           cudaStream_t s) {
@@ -439,9 +557,17 @@ int aw_launch_grid_region(const aw_plan *p, const aw_kernel_set *k, const void *
         a.passes = ((rc.S / a.M) * rc.S + 31) / 32;
         int r;
         const int st = k->spec.storage;
-        if (st == AW_STORAGE_FP32) r = launch_region_t<AW_STORAGE_FP32>(a, rc.BT, sms, s);
-        else if (st == AW_STORAGE_BF16) r = launch_region_t<AW_STORAGE_BF16>(a, rc.BT, sms, s);
-        else r = launch_region_t<AW_STORAGE_FP16>(a, rc.BT, sms, s);
+        if (p->npol == 4) {
+            if (st == AW_STORAGE_FP32) r = launch_region_t<AW_STORAGE_FP32, 4, 1>(a, rc.BT, sms, s);
+            else if (st == AW_STORAGE_BF16) r = launch_region_t<AW_STORAGE_BF16, 4, 1>(a, rc.BT, sms, s);
+            else r = launch_region_t<AW_STORAGE_FP16, 4, 1>(a, rc.BT, sms, s);
+        } else if (a.passes <= 2) {
+            r = launch_region1<2>(a, st, rc.BT, sms, s);
+        } else if (a.passes <= 8) {
+            r = launch_region1<8>(a, st, rc.BT, sms, s);
+        } else {
+            r = launch_region1<RG_TPL1>(a, st, rc.BT, sms, s);
+        }
         if (r) return r;
     }
     return AW_OK;

@@ -242,7 +242,7 @@ int aw_launch_grid(const aw_grid_launch &L);
 // every support's item list on stream s.
 int aw_region_tile(int S, int npol);
 int aw_region_rows(int S);
-int aw_region_threads(int S);
+int aw_region_threads(int S, int npol);
 int aw_launch_grid_region(const aw_plan *p, const aw_kernel_set *k, const void *vis, const float *weight, void *grid,
                           cudaStream_t s);
 int aw_region_bounds_status(unsigned int *v, int reset);

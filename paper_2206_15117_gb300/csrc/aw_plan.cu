@@ -495,7 +495,7 @@ static int build_region(aw_plan *plan, const aw_kernel_set *ks, int64_t nv, uint
     for (int b = 0; b < nb; ++b) {
         const int S = ks->bin_support[(size_t)b], T = aw_region_tile(S, plan->npol);
         const bool low = (b / per_plane) % plan->nw < split;
-        bt[(size_t)b] = (T && low) ? (T | aw_region_threads(S) / 32 << 8) : 0;
+        bt[(size_t)b] = (T && low) ? (T | aw_region_threads(S, plan->npol) / 32 << 8) : 0;
     }
     DevBuf dbt, dcnt;
     AW_CUDA_TRY(aw_dev_malloc(&dbt.p, sizeof(int32_t) * std::max(nb, 1)));
@@ -543,7 +543,7 @@ static int build_region(aw_plan *plan, const aw_kernel_set *ks, int64_t nv, uint
             aw_plan::RegionClass c;
             c.S = kv.first;
             c.T = aw_region_tile(c.S, plan->npol);
-            c.BT = aw_region_threads(c.S);
+            c.BT = aw_region_threads(c.S, plan->npol);
             c.n = (int64_t)kv.second.size();
             plan->rclasses.push_back(c);
             AW_CUDA_TRY(aw_dev_malloc(&plan->rclasses.back().d_items, sizeof(int4) * kv.second.size()));

@@ -25,7 +25,7 @@ SCRIPT = textwrap.dedent('''
     from paper_2206_15117_gb300 import aw
     from paper_2206_15117_gb300 import synthetic as sy
     from oracle import core as oc
-    from tests.gpu_cases import case_fullpol, case_stokes_i_cfg1, rel_err, used_bins
+    from tests.gpu_cases import case_fullpol, case_stokes_i_cfg1, case_wproj, rel_err, used_bins
     assert aw.load()._name.endswith("libaw_checked.so"), aw.load()._name
     aw.aw_debug_bounds_status(reset=True)
     ctx = aw.aw_create(0)
@@ -35,7 +35,8 @@ SCRIPT = textwrap.dedent('''
                                                  (32, 256, 2, 256, 3)]),
              ("fullpol_wide", case_fullpol(n_t=200, radius=60.0, supports=(16, 40, 56)), [(32, 256, 2, 256, 3)]),
              ("stokes_i", case_stokes_i_cfg1(time_samples=20), [(16, 128, 2, 0, 0), (32, 256, 2, 256, 1),
-                                                              (16, 128, 3, 256, 2, 1)])]
+                                                              (16, 128, 3, 256, 2, 1)]),
+             ("wproj_region", case_wproj(vis_fraction=0.001), [(32, 256, 2, 256, 3), (32, 256, 2, 256, 3, 14)])]
     for name, (ob, kw), tunes in cases:
         npol, N = kw["npol"], kw["N"]
         kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
@@ -81,6 +82,7 @@ def test_bounds_checked_build_reports_no_bad_index():
     rep = json.loads(line[len("REPORT "):])
     assert rep["status"] == 0, rep
     assert rep["fullpol"] < 1e-5 and rep["stokes_i"] < 1e-5 and rep["fullpol_wide"] < 1e-5, rep
+    assert rep["wproj_region"] < 1e-5, rep
 
 
 def test_normal_build_has_no_bounds_checks():

@@ -253,16 +253,24 @@ def test_hybrid_schedule_grid(ctx, which, split):
 # tile) against the same oracle: full-pol cases whose supports all fit a region,
 # one that mixes region supports with a support too wide for it (its bins take
 # OFFSETS), a dense case whose tiles hold more visibilities than one staging
-# round and one work item, and Stokes I (every bin on OFFSETS); direct and
-# graph-captured, with BF16 / FP16 tables on the mixed case.
-@pytest.mark.parametrize("which", ["fullpol", "mixed_supports", "dense", "wproj"])
+# round and one work item, and Stokes-I w-projection (the one-value-a-tap form
+# of the kernel for supports 8-48; 56-64 on OFFSETS beside it), all planes or
+# the first 14 on the region kernel; direct and graph-captured, with BF16 /
+# FP16 tables on the mixed and Stokes-I cases.
+@pytest.mark.parametrize("which", ["fullpol", "mixed_supports", "dense", "wproj", "wproj_split"])
 def test_region_schedule_grid(ctx, which):
     from paper_2206_15117_gb300 import aw
     ob, kw = {"fullpol": case_fullpol,
               "mixed_supports": lambda: case_fullpol(supports=(16, 40, 56), n_t=30),
               "dense": lambda: case_fullpol(n_t=600, radius=50.0, supports=(16, 24, 32)),
-              "wproj": lambda: case_wproj(vis_fraction=0.002)}[which]()
-    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_REGION))
+              "wproj": lambda: case_wproj(vis_fraction=0.002),
+              "wproj_split": lambda: case_wproj(vis_fraction=0.002)}[which]()
+    split = 14 if which == "wproj_split" else 0
+    c = Case(ctx, ob, kw, tune=aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_REGION, split))
+    info = aw.aw_plan_query(c.plan)
+    assert info.region_lists > 0
+    if which.startswith("wproj"):
+        assert info.grid_kernels == info.region_lists + 1   # the wide (or later) planes on OFFSETS
     _check_grid(c)
     _check_grid(c, batched=True)
     _check_grid(c, batched=True)  # the cached graph again
@@ -276,10 +284,11 @@ def test_region_schedule_grid(ctx, which):
         assert np.unique(key, return_counts=True)[1].max() > 1024
 
 
+@pytest.mark.parametrize("which", ["fullpol", "wproj"])
 @pytest.mark.parametrize("storage,tol", [(1, 4e-3), (2, 5e-4)])
-def test_region_schedule_reduced_precision(ctx, storage, tol):
+def test_region_schedule_reduced_precision(ctx, storage, tol, which):
     from paper_2206_15117_gb300 import aw
-    ob, kw = case_fullpol(supports=(16, 40, 56), n_t=30)
+    ob, kw = case_fullpol(supports=(16, 40, 56), n_t=30) if which == "fullpol" else case_wproj(vis_fraction=0.002)
     c = Case(ctx, ob, kw, storage=storage, tune=aw.aw_tune(32, 256, 2, 256, aw.AW_GRID_REGION))
     g, _ = c.gpu_grid(batched=True)
     G, _, _ = c.oracle_grid()
