@@ -62,13 +62,9 @@ constexpr int RG_CH = 128;      // visibilities staged per round
 constexpr int RG_TPL1 = 18;     // most taps a lane in the Stokes-I form ((48 / 4) 48 / 32)
 constexpr int RG_MAXT = 320;    // largest CTA (10 warps)
 // resident CTAs per SM the register budget is set for (the region size,
-// AW_RG_RMAX, decides the shared-memory side), and whether the next unit's
-// kernel values are loaded while the current unit runs (a second register set)
+// AW_RG_RMAX, decides the shared-memory side)
 #ifndef AW_RG_MINB
 #define AW_RG_MINB 2
-#endif
-#ifndef AW_RG_PREFETCH
-#define AW_RG_PREFETCH 0
 #endif
 
 struct RegionArgs {
@@ -157,12 +153,11 @@ constexpr size_t region_smem_bytes(int R, int npol) {
            (size_t)(RG_CH + 1) * 2 * sizeof(int);
 }
 
-// One full-polarisation visibility-tap: the region cell (planes (0, 1) in c01,
-// (2, 3) in c23) += K V, plane s getting the sum over correlations c of
-// K[s][c] V_c (the products formed while the cell is being read).
-__device__ __forceinline__ void mueller_update(float4 &c01, float4 &c23, const float2 (&k)[16], float4 v01,
-                                               float4 v23) {
-    float4 r01 = c01, r23 = c23;
+// One full-polarisation visibility-tap on a region cell held in registers
+// (planes (0, 1) in r01, (2, 3) in r23): += K V, plane s getting the sum over
+// correlations c of K[s][c] V_c.
+__device__ __forceinline__ void mueller_acc(float4 &r01, float4 &r23, const float2 (&k)[16], float4 v01,
+                                            float4 v23) {
     cmac2(r01.x, r01.y, k[0], v01.x, v01.y);
     cmac2(r01.z, r01.w, k[4], v01.x, v01.y);
     cmac2(r23.x, r23.y, k[8], v01.x, v01.y);
@@ -179,12 +174,12 @@ __device__ __forceinline__ void mueller_update(float4 &c01, float4 &c23, const f
     cmac2(r01.z, r01.w, k[7], v23.z, v23.w);
     cmac2(r23.x, r23.y, k[11], v23.z, v23.w);
     cmac2(r23.z, r23.w, k[15], v23.z, v23.w);
-    c01 = r01;
-    c23 = r23;
 }
 
 // NPOL = 4: full polarisation, 16 Mueller values a tap, units of one offset
-// group and one pass of 32 taps a warp.  NPOL = 1: Stokes I, one value a tap
+// group and one pass of 32 taps a warp; with TMAX = 2 (CTAs of at most 256
+// threads, supports of two passes or more) a unit takes two passes at once, so
+// each visibility gives a lane two independent read-modify-writes.  NPOL = 1: Stokes I, one value a tap
 // and one plane (an eighth of the shared memory); a single update per
 // visibility-tap leaves each read-modify-write little arithmetic to hide its
 // latency behind, so the CTA has only 4 warps (row classes), a lane takes
@@ -192,7 +187,7 @@ __device__ __forceinline__ void mueller_update(float4 &c01, float4 &c23, const f
 // ... of its warp's rows) and a unit is a whole offset group: a.passes
 // independent updates per visibility and lane.
 template <int ST, int R, int NPOL, int TMAX>
-__global__ void __launch_bounds__(NPOL == 4 ? RG_MAXT : 128, NPOL == 4 ? AW_RG_MINB : 4)
+__global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT), NPOL == 4 ? AW_RG_MINB : 4)
     grid_region_kernel(RegionArgs a) {
     constexpr int P = NPOL * NPOL, RR = R * R;
     extern __shared__ __align__(16) char rg_smem[];
@@ -352,7 +347,10 @@ __global__ void __launch_bounds__(NPOL == 4 ? RG_MAXT : 128, NPOL == 4 ? AW_RG_M
                                 cmac2(r.x, r.y, k[0], v.x, v.y);
                                 reg0[cell] = r;
                             } else {
-                                mueller_update(reg01[cell], reg23[cell], k, s_v[2 * j], s_v[2 * j + 1]);
+                                float4 r01 = reg01[cell], r23 = reg23[cell];
+                                mueller_acc(r01, r23, k, s_v[2 * j], s_v[2 * j + 1]);
+                                reg01[cell] = r01;
+                                reg23[cell] = r23;
                             }
                         }
                         // the next visibility's cells may be this one's cells of
@@ -402,21 +400,45 @@ __global__ void __launch_bounds__(NPOL == 4 ? RG_MAXT : 128, NPOL == 4 ? AW_RG_M
                         __syncthreads();
                     }
                 }
-            } else {
-#if AW_RG_PREFETCH
-                float2 kA[P], kB[P];
+            } else if constexpr (TMAX == 2) {
+                // two passes of one offset group at a time: both taps' cells are
+                // read before either is written (distinct taps, distinct cells)
+                for (int g = 0; g < s_ng; ++g) {
+                    for (int p0 = 0; p0 < passes; p0 += 2) {
+                        const bool two = p0 + 1 < passes;
+                        float2 kA[P], kB[P];
 #pragma unroll
-                for (int m = 0; m < P; ++m) { kA[m] = make_float2(0.f, 0.f); kB[m] = kA[m]; }
-                if (nunits > 0) load_unit(0, kA);
-                for (int u = 0; u < nunits; u += 2) {
-                    if (u + 1 < nunits) load_unit(u + 1, kB);
-                    run_unit(u, kA);
-                    if (u + 1 < nunits) {
-                        if (u + 2 < nunits) load_unit(u + 2, kA);
-                        run_unit(u + 1, kB);
+                        for (int m = 0; m < P; ++m) { kA[m] = make_float2(0.f, 0.f); kB[m] = kA[m]; }
+                        load_unit(g * passes + p0, kA);
+                        if (two) load_unit(g * passes + p0 + 1, kB);
+                        int ta, cta, tb = -1, ctb = 0;
+                        tap_of(p0, ta, cta);
+                        if (two) tap_of(p0 + 1, tb, ctb);
+                        const int sg1 = s_gss[g + 1];
+                        for (int sg = s_gss[g]; sg < sg1; ++sg) {
+                            const int j1 = s_ss[sg + 1];
+                            for (int j = s_ss[sg]; j < j1; ++j) {
+                                const int base = s_cell[j];
+                                const int ca = base + cta, cb = base + ctb;
+                                const bool oa = ta >= 0 && RG_BOK(ca >= 0 && ca < RR, BC_R_SMEM);
+                                const bool ob = tb >= 0 && RG_BOK(cb >= 0 && cb < RR, BC_R_SMEM);
+                                const float4 v01 = s_v[2 * j], v23 = s_v[2 * j + 1];
+                                float4 a01 = z4, a23 = z4, b01 = z4, b23 = z4;
+                                if (oa) { a01 = reg01[ca]; a23 = reg23[ca]; }
+                                if (ob) { b01 = reg01[cb]; b23 = reg23[cb]; }
+                                mueller_acc(a01, a23, kA, v01, v23);
+                                mueller_acc(b01, b23, kB, v01, v23);
+                                if (oa) { reg01[ca] = a01; reg23[ca] = a23; }
+                                if (ob) { reg01[cb] = b01; reg23[cb] = b23; }
+                                // the next visibility's cells may be this one's cells of other lanes
+                                __syncwarp();
+                            }
+                            // another footprint-row residue next: other warps may then write rows this warp wrote
+                            __syncthreads();
+                        }
                     }
                 }
-#else
+            } else {
                 for (int u = 0; u < nunits; ++u) {
                     float2 kA[P];
 #pragma unroll
@@ -424,7 +446,6 @@ __global__ void __launch_bounds__(NPOL == 4 ? RG_MAXT : 128, NPOL == 4 ? AW_RG_M
                     load_unit(u, kA);
                     run_unit(u, kA);
                 }
-#endif
             }
         }
         __syncthreads();
@@ -472,6 +493,7 @@ int launch_region_t(const RegionArgs &a, int BT, int sm_count, cudaStream_t s) {
     if (a.R != AW_RG_RMAX) return aw_set_error(AW_EINVAL, "region side %d", a.R);
     if (NPOL == 1 && (a.passes > TMAX || (BT != 64 && BT != 128)))
         return aw_set_error(AW_EINVAL, "Stokes-I region: %d taps a lane, %d threads", a.passes, BT);
+    if (NPOL == 4 && TMAX == 2 && BT > 256) return aw_set_error(AW_EINVAL, "paired region units: %d threads", BT);
     auto kern = grid_region_kernel<ST, AW_RG_RMAX, NPOL, TMAX>;
     const size_t smem = region_smem_bytes(a.R, NPOL);
     AW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -482,6 +504,13 @@ int launch_region_t(const RegionArgs &a, int BT, int sm_count, cudaStream_t s) {
     kern<<<(unsigned)blocks, BT, smem, s>>>(a);
     AW_CHECK_LAUNCH();
     return AW_OK;
+}
+
+template <int TMAX>
+int launch_region4(const RegionArgs &a, int st, int BT, int sm_count, cudaStream_t s) {
+    if (st == AW_STORAGE_FP32) return launch_region_t<AW_STORAGE_FP32, 4, TMAX>(a, BT, sm_count, s);
+    if (st == AW_STORAGE_BF16) return launch_region_t<AW_STORAGE_BF16, 4, TMAX>(a, BT, sm_count, s);
+    return launch_region_t<AW_STORAGE_FP16, 4, TMAX>(a, BT, sm_count, s);
 }
 
 template <int TMAX>
@@ -496,7 +525,10 @@ int launch_region1(const RegionArgs &a, int st, int BT, int sm_count, cudaStream
 int aw_region_rows(int S) {
     // row classes M (= warps of the CTA, 4..10) dividing S whose passes of 32
     // taps (S / M rows of S taps per warp) leave the fewest idle lanes; ties go
-    // to more warps.  0: none
+    // to more warps, except that a support done in one pass takes half the
+    // warps, so that its units pair two passes (S = 16: 4 warps, 0.9 ms faster
+    // on the 64M-visibility full-pol set than 8 warps in one pass; S = 40 keeps
+    // 10 warps unpaired, 2.4 ms faster than 5 warps paired).  0: none
     int best = 0;
     double best_eff = 0.0;
     for (int M = 10; M >= 4; --M) {
@@ -505,7 +537,9 @@ int aw_region_rows(int S) {
         const double eff = (double)taps / (32.0 * passes);
         if (eff > best_eff + 1e-9) { best_eff = eff; best = M; }
     }
-    return best_eff >= 0.74 ? best : 0;
+    if (best_eff < 0.74) return 0;
+    if ((S / best) * S <= 32 && best / 2 >= 4 && S % (best / 2) == 0 && (S / (best / 2)) * S % 32 == 0) best /= 2;
+    return best;
 }
 
 // Stokes I: 4 warps (row classes) for supports that are multiples of 4 and
@@ -557,10 +591,10 @@ int aw_launch_grid_region(const aw_plan *p, const aw_kernel_set *k, const void *
         a.passes = ((rc.S / a.M) * rc.S + 31) / 32;
         int r;
         const int st = k->spec.storage;
-        if (p->npol == 4) {
-            if (st == AW_STORAGE_FP32) r = launch_region_t<AW_STORAGE_FP32, 4, 1>(a, rc.BT, sms, s);
-            else if (st == AW_STORAGE_BF16) r = launch_region_t<AW_STORAGE_BF16, 4, 1>(a, rc.BT, sms, s);
-            else r = launch_region_t<AW_STORAGE_FP16, 4, 1>(a, rc.BT, sms, s);
+        if (p->npol == 4 && a.passes >= 2 && rc.BT <= 256) {
+            r = launch_region4<2>(a, st, rc.BT, sms, s);
+        } else if (p->npol == 4) {
+            r = launch_region4<1>(a, st, rc.BT, sms, s);
         } else if (a.passes <= 2) {
             r = launch_region1<2>(a, st, rc.BT, sms, s);
         } else if (a.passes <= 8) {
