@@ -584,8 +584,8 @@ int mosaic_gamma(aw_ctx *ctx, const float *beams, int32_t nfield, int32_t N, flo
  * Limit: N * N <= 4096 * 4096 pixels; larger images return AW_EINVAL before
  * any GPU work.  The first call on a device (and the first after its context
  * is re-created, e.g. by cudaDeviceReset) looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and
+ * (cudaGetSymbolAddress) with that device current.  Every call shares the one
+ * array and
  * nothing in it needs to start at zero (each pass reads only slots written
  * earlier in the same call), but calls whose GPU work overlaps (different
  * streams or host threads) race on it: serialise them.  beams: device float
