@@ -1217,11 +1217,11 @@ def run_ours(args, rank, world, dist):
     peak_tflops, peak_src = fp32_peak_tflops(dev_index)
     achieved = flops / (dom_ms / 1e3) / 1e12
     # DRAM bytes per launch of the dominant kernel: the one-bin-pair ncu capture summarised in
-    # profiles/dram_traffic_fullpol_aw_1pair.md (1,139,896 visibilities: region gridding 146.6 MB,
-    # degridding 96.7 MB), scaled to this workload by the visibility count (the per-visibility bytes
+    # profiles/dram_traffic_fullpol_aw_1pair.md (1,139,896 visibilities: region gridding 146.5 MB,
+    # degridding 96.5 MB), scaled to this workload by the visibility count (the per-visibility bytes
     # scale; the tables touched per visibility grow with the bins, so this is a lower bound).  Only
     # for the region schedule and the degridder at full size; null otherwise.
-    per_vis = {"region": 146.6e6 / 1139896, "degrid_items_kernel": 96.7e6 / 1139896}
+    per_vis = {"region": 146.5e6 / 1139896, "degrid_items_kernel": 96.5e6 / 1139896}
     traffic = None
     if not args.subset:
         if g_ms >= d_ms and tune.grid_mode == aw.AW_GRID_REGION:
