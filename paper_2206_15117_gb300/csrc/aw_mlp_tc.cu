@@ -231,8 +231,8 @@ __device__ __forceinline__ float warp_colsum(float (&v)[CW], int lane) {
 // run the epilogue of tile i the tensor cores multiply tile i + 1 and tile
 // i + 2 loads.  Warp w reads accumulator lanes 32 (w mod 4) .. + 31 (its 32
 // rows), columns 32 (w div 4) .. + 31 (all columns for N <= 32, where warps
-// 4-15 only stage).  The transposed output leaves through shared memory as
-// 256-byte column runs.
+// 4-15 only stage).  The outputs leave through padded shared memory as whole
+// rows.
 template <int EPI, int N, int KT>
 __global__ void __launch_bounds__(512, 1) tc_tall_kernel(TallArgs g) {
     constexpr int TILE_A = 128 * KT * 2, TILE_B = N * KT * 2;
@@ -425,7 +425,7 @@ struct RedArgs {
     const __half *Bw;     // [K][N] row-major: likewise
     int64_t K;            // batch size (multiple of 128)
     float *out;           // += scale C (out[r][c], or out[c][r] when transpose), columns c < ncols
-    float *outb;          // BIAS: += scale times the row sums of A
+    float *outb;          // BIAS: += scale times the column sums of A (over the batch)
     int ncols, transpose, ldo;
     float scale;
     unsigned int *err;
@@ -808,9 +808,9 @@ static int launch_tall(const TallArgs &g, int sms, cudaStream_t st) {
     return AW_OK;
 }
 
-// C[128][N] = A B^T over the batch added to out (scaled, columns < ncols,
-// optionally transposed; with BIAS the row sums of A added to outb): one CTA
-// per SM, each a slice of the batch.
+// C[128][N] = A^T B over the batch (A [K][128], B [K][N]) added to out
+// (scaled, columns < ncols, optionally transposed; with BIAS the column sums
+// of A added to outb): one CTA per SM, each a slice of the batch.
 template <int N, bool BIAS>
 static int launch_red(const RedArgs &g, int slices, cudaStream_t st) {
     constexpr int NB = N + (BIAS ? 16 : 0);
