@@ -528,7 +528,8 @@ int aw_region_rows(int S) {
     // to more warps, except that a support done in one pass takes half the
     // warps, so that its units pair two passes (S = 16: 4 warps, 0.9 ms faster
     // on the 64M-visibility full-pol set than 8 warps in one pass; S = 40 keeps
-    // 10 warps unpaired, 2.4 ms faster than 5 warps paired).  0: none
+    // 10 warps unpaired, 2.4 ms faster than 5 warps paired and 1.7 ms faster
+    // than 8 warps paired).  0: none
     int best = 0;
     double best_eff = 0.0;
     for (int M = 10; M >= 4; --M) {
