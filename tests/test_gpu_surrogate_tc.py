@@ -28,7 +28,7 @@ def ctx():
     return aw.aw_create(0)
 
 
-@pytest.mark.parametrize("npol,n_hidden", [(4, 4), (1, 3)])
+@pytest.mark.parametrize("npol,n_hidden", [(4, 4), (1, 3), (4, 2)])
 def test_tensor_core_gradient_matches_fp64_oracle(ctx, npol, n_hidden):
     from paper_2206_15117_gb300 import aw
     omega0 = 30.0
