@@ -59,6 +59,9 @@ def parse():
                     help="skip the full configuration-5 mosaic (7 fields x 10M visibilities)")
     ap.add_argument("--learned-inline-case", type=int, default=None, metavar="ENGINE",
                     help="only run the small inline-surrogate profiling case on engine 0 (mma.sync) or 1 (tcgen05)")
+    ap.add_argument("--wproj-case", type=int, default=None, metavar="REPS",
+                    help="only grid and degrid configuration 2 (Stokes-I w-projection, FP32 tables, region schedule "
+                         "with planes 0-17) REPS times: the profiling case of that configuration")
     ap.add_argument("--learned-train-case", type=int, default=None, metavar="STEPS",
                     help="only run the small surrogate-training profiling case for STEPS steps")
     ap.add_argument("--no-clean", action="store_true", help="skip the Cotton-Schwab cleaning measurement")
@@ -985,6 +988,50 @@ def learned_degrid(ctx, dev, args, kw, kw_fine, vd, obs, stream, timed, kmax, ch
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def wproj_case(reps: int):
+    """Configuration 2 for profiling: 20.16M Stokes-I visibilities, 2048^2, 32 w planes (supports 8-64),
+    OS 8, FP32 tables; the region schedule with planes 0-17 on the region kernel (the bench's choice for
+    this configuration); one untimed grid + degrid, then `reps` timed ones."""
+    import torch
+    from paper_2206_15117_gb300 import aw
+    from paper_2206_15117_gb300 import build as awbuild
+    from paper_2206_15117_gb300 import synthetic as sy
+    awbuild.build()
+    ctx = aw.aw_create(0)
+    dev = torch.device("cuda", 0)
+    ob = sy.observation(2)
+    kw = sy.config_spec(2, ob)
+    N = kw["N"]
+    kg = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_GRID)
+    kd = aw.aw_make_kernels(ctx, **kw, role=aw.AW_ROLE_DEGRID)
+    vd, keep = aw.device_observation(ob, dev)
+    plan = aw.aw_plan_create(ctx, vd, kg, tune=aw.aw_tune(32, 256, 2, 1024, aw.AW_GRID_REGION, 18))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    vis = torch.randn((ob.nvis, 1), dtype=torch.complex64, device=dev, generator=gen)
+    model = torch.randn((1, N, N), dtype=torch.complex64, device=dev, generator=gen)
+    out = torch.empty_like(vis)
+    grid = torch.zeros((1, N, N), dtype=torch.complex64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    gms, dms = [], []
+    for r in range(reps + 1):
+        grid.zero_()
+        ev[0].record()
+        aw.aw_grid_batched(ctx, plan, kg, vis, None, grid)
+        ev[1].record()
+        aw.aw_degrid(ctx, plan, kd, model, out)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if r:
+            gms.append(ev[0].elapsed_time(ev[1]))
+            dms.append(ev[1].elapsed_time(ev[2]))
+    info = aw.aw_plan_query(plan)
+    print(json.dumps({"case": "wproj", "nvis": int(ob.nvis), "mean_taps": float(info.mean_taps), "reps": reps,
+                      "grid_ms": statistics.median(gms) if gms else None,
+                      "degrid_ms": statistics.median(dms) if dms else None}))
+    return 0
+
+
 def learned_train_case(steps: int):
     """A small case for profiling surrogate training on the tensor cores: an exact full-pol set of
     512^2 x 4, 4 w planes (supports 8, 8, 12, 16), OS 8, one PA and frequency bin; a 5 -> 128 x 4 -> 32
@@ -1492,6 +1539,8 @@ def main():
         return learned_inline_case(args.learned_inline_case)
     if args.learned_train_case is not None:
         return learned_train_case(args.learned_train_case)
+    if args.wproj_case is not None:
+        return wproj_case(args.wproj_case)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

@@ -544,8 +544,10 @@ __device__ __forceinline__ void smem_krow(const char *slab, int tl, int c, float
 // visibility first, then apply the kernel one Mueller row at a time.  Partial
 // sums (AW_DG_VB x NPOL complex per lane) are reduce-scattered over the warp
 // and summed across the group's warps in shared memory.
+// Stokes I: at most 64 registers, four CTAs per SM (the kernel hides the
+// latency of its grid loads with resident warps).
 template <int NPOL, int ST, bool SUB>
-__global__ void __launch_bounds__(256, 2) degrid_items_kernel(DegridArgs a) {
+__global__ void __launch_bounds__(256, NPOL == 1 ? 4 : 2) degrid_items_kernel(DegridArgs a) {
     constexpr int P = NPOL * NPOL;
     constexpr int VB = AW_DG_VB;
     constexpr int NV = VB * NPOL * 2;  // partial sums per lane

@@ -145,12 +145,12 @@ __device__ __forceinline__ void cmac2(float &re, float &im, float2 k, float vr, 
     im = fmaf(k.y, vr, im);
 }
 
-// Shared memory of one CTA: the region (R^2 cells of NPOL complex FP32
-// accumulators), the staged visibilities (NPOL complex each) and four int
-// arrays of the round.
+// Shared memory of one CTA: the region (R rows of NPOL complex FP32
+// accumulators per cell, R cells a row plus two of padding for Stokes I), the
+// staged visibilities (NPOL complex each) and four int arrays of the round.
 constexpr size_t region_smem_bytes(int R, int npol) {
-    return (size_t)R * R * npol * 8 + (size_t)RG_CH * npol * 8 + (size_t)RG_CH * 2 * sizeof(int) +
-           (size_t)(RG_CH + 1) * 2 * sizeof(int);
+    return (size_t)R * (npol == 1 ? R + 2 : R) * npol * 8 + (size_t)RG_CH * npol * 8 +
+           (size_t)RG_CH * 2 * sizeof(int) + (size_t)(RG_CH + 1) * 2 * sizeof(int);
 }
 
 // One full-polarisation visibility-tap on a region cell held in registers
@@ -189,7 +189,11 @@ __device__ __forceinline__ void mueller_acc(float4 &r01, float4 &r23, const floa
 template <int ST, int R, int NPOL, int TMAX>
 __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT), NPOL == 4 ? AW_RG_MINB : 4)
     grid_region_kernel(RegionArgs a) {
-    constexpr int P = NPOL * NPOL, RR = R * R;
+    // row stride of the region in cells: Stokes I pads two cells, so that region
+    // rows 4 apart (the row classes of one pass of a half-warp) fall on the other
+    // half of the shared-memory banks (8-byte cells, 4 rows of 58 cells = 464 words)
+    constexpr int RS = NPOL == 1 ? R + 2 : R;
+    constexpr int P = NPOL * NPOL, RR = R * RS;
     extern __shared__ __align__(16) char rg_smem[];
     const int S = a.S, L = S * S, M = a.M, passes = a.passes;
     // NPOL 4: planes (0, 1) and (2, 3) of a cell as two float4; NPOL 1: one float2
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT),
     char *after_region = rg_smem + (size_t)RR * NPOL * 8;
     float4 *s_v = reinterpret_cast<float4 *>(after_region);     // NPOL 4: [RG_CH][2]
     float2 *s_v1 = reinterpret_cast<float2 *>(after_region);    // NPOL 1: [RG_CH]
-    int *s_cell = reinterpret_cast<int *>(after_region + (size_t)RG_CH * NPOL * 8);   // [RG_CH] ly * R + lx
+    int *s_cell = reinterpret_cast<int *>(after_region + (size_t)RG_CH * NPOL * 8);   // [RG_CH] ly * RS + lx
     int *s_key = s_cell + RG_CH;                                // [RG_CH] offset * 64 + ly mod M
     int *s_ss = s_key + RG_CH;                                  // [RG_CH + 1] sub-group starts
     int *s_gss = s_ss + RG_CH + 1;                              // [RG_CH + 1] first sub-group of each group
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT),
                 }
                 const int ly = (int)r.y0 - oy, lx = (int)r.x0 - ox;
                 const bool inr = RG_BOK(ly >= 0 && lx >= 0 && ly + S <= R && lx + S <= R, BC_R_CELL);
-                s_cell[tid] = inr ? ly * R + lx : 0;
+                s_cell[tid] = inr ? ly * RS + lx : 0;
                 s_key[tid] = ((int)r.fy * a.OS + (int)r.fx) * 64 + (inr ? ly % M : 0);
             }
             __syncthreads();
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT),
                 const int lr = q / S;
                 const int tx = q - lr * S, ty = warp + lr * M;
                 t = (ty < S) ? ty * S + tx : -1;
-                ct = ty * R + tx;
+                ct = ty * RS + tx;
             };
             auto load_unit = [&](int u, float2 (&k)[P]) {
                 const int g = u / passes;
@@ -375,7 +379,7 @@ __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT),
                         const int q = lane + 32 * i;
                         const int lr = q / S, tx = q - lr * S, ty = warp + lr * M;
                         const bool on = i < tpl && q < tw && kok;
-                        ct[i] = on ? ty * R + tx : -1;
+                        ct[i] = on ? ty * RS + tx : -1;
                         k[i] = on ? rg_k1<ST>(a.ktab, kb, ty * S + tx) : make_float2(0.f, 0.f);
                     }
                     const int sg1 = s_gss[g + 1];
@@ -451,7 +455,8 @@ __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT),
         __syncthreads();
         // ---- add the region to the grid (cells that received nothing are skipped)
         for (int c = tid; c < RR; c += BT) {
-            const int cy = c / R, cx = c - cy * R;
+            const int cy = c / RS, cx = c - cy * RS;
+            if (cx >= R) continue;   // row padding
             const int gy = oy + cy, gx = ox + cx;
             if constexpr (NPOL == 1) {
                 const float2 v = reg0[c];
