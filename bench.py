@@ -280,7 +280,9 @@ def workload_config(ob, kw, info):
                        "supports 16-72, OS 8, 288 channels of uneven counts",
            "nvis": int(ob.nvis), "N": kw["N"], "npol": 4, "nbins": 32 * len(kw["pa"]) * len(kw["fbin_freqs"]),
            "OS": kw["OS"], "supports": list(kw["supports"]),
-           "l2": "inputs larger than L2 (visibilities 2 GB, kernel tables 33 GB)"}
+           "l2": "inputs larger than L2 (visibilities 2 GB, kernel tables 33 GB)",
+           "weights": "natural: the timed steps pass no weight array (the weighted gridding call is timed "
+                      "separately, weighted_grid)"}
     if info is not None:
         cfg.update({"nvalid": int(info.nvalid), "mean_taps": round(info.mean_taps, 1),
                     "tile": info.tile, "chunk": info.chunk})
@@ -1321,6 +1323,29 @@ def run_ours(args, rank, world, dist):
             torch.cuda.empty_cache()
     alt_plans = []
 
+    # the weighted path: the timed steps pass no weight array (natural weights:
+    # nothing read); here one gridding call with per-visibility, per-correlation
+    # FP32 weights ([nvis][4], 16 B per visibility read by the gridder)
+    wgen = torch.Generator(device=dev)
+    wgen.manual_seed(7)
+    wts = torch.rand((nvis, 4), dtype=torch.float32, device=dev, generator=wgen) + 0.5
+    wms = []
+    for r_ in range(4):
+        grid.zero_()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        aw.aw_grid_batched(ctx, plan, kg, vis, wts, grid)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        if r_:
+            wms.append(a_.elapsed_time(b_))
+    weighted = {"grid_ms": statistics.median(wms), "grid_ms_natural": g_ms,
+                "weight_bytes": int(wts.numel() * 4),
+                "note": "the same gridding call with a [nvis][4] FP32 weight array; the timed steps use natural "
+                        "weights (no weight array passed, none read)"}
+    del wts
+    torch.cuda.empty_cache()
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
@@ -1449,6 +1474,7 @@ def run_ours(args, rank, world, dist):
                 "config": workload_config(ob, kw, info),
                 "parallelism": "replicas" if world > 1 else "single",
                 "breakdown_ms": {"grid": g_ms, "fft_to_image": statistics.mean(t_fft), "degrid": d_ms},
+                "weighted_grid": weighted,
                 "once_per_dataset_s": {"kernel_synthesis_grid_and_degrid": t_synth, "autotune": t_tune,
                                        "plan_sort": t_plan, "table_bytes_per_set": int(kinfo.bytes)},
                 "cold": {"value": nvis * world / (t_synth + t_tune + t_plan + ms_per_step / 1e3) / 1e6, "unit": UNIT,
