@@ -404,8 +404,9 @@ int aw_fft_to_image(aw_ctx *ctx, const aw_kernel_set *kset, void *grid, double w
  *   Parameters: one flat FP32 vector, per layer W [out][in] then b [out].
  *   Loss (1/B) sum (y - t)^2; Adam (b1 0.9, b2 0.999, eps 1e-8) with bias
  *   correction and a cosine learning-rate decay from lr to lr_final.
- * Training runs in the library's kernels with FP32 master weights; the
- * inline evaluation uses an FP16 copy of the weights with FP32 accumulation.
+ * Training runs in the library's kernels with FP32 master weights (on the
+ * tensor cores for width 128: aw_surrogate_set_train_engine); the inline
+ * evaluation uses an FP16 copy of the weights with FP32 accumulation.
  */
 typedef struct aw_surrogate_cfg {
     int32_t npol;            /* 1 or 4                                           */
