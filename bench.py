@@ -714,7 +714,7 @@ def learned_section(ctx, dev, args):
     exact = aw.aw_make_kernels(ctx, **kw)
     t_synth = time.perf_counter() - t0
     # 4x finer w sampling: the training set of the network and the reference
-    # the two gridding paths are judged against
+    # the two gridding paths are compared against
     kw_fine = {**kw, "nw": 128, "supports": sy.w_supports(128)}
     fine = aw.aw_make_kernels(ctx, **kw_fine)
     S0 = kw["supports"][0]
