@@ -177,9 +177,10 @@ __device__ __forceinline__ void mueller_acc(float4 &r01, float4 &r23, const floa
 }
 
 // NPOL = 4: full polarisation, 16 Mueller values a tap, units of one offset
-// group and one pass of 32 taps a warp; with TMAX = 2 (CTAs of at most 256
-// threads, supports of two passes or more) a unit takes two passes at once, so
-// each visibility gives a lane two independent read-modify-writes.  NPOL = 1: Stokes I, one value a tap
+// group and one pass of 32 taps a warp; with TMAX = 2 or 3 (CTAs of at most
+// 256 or 192 threads, supports of two or three passes or more) a unit takes
+// TMAX passes at once, so each visibility gives a lane TMAX independent
+// read-modify-writes.  NPOL = 1: Stokes I, one value a tap
 // and one plane (an eighth of the shared memory); a single update per
 // visibility-tap leaves each read-modify-write little arithmetic to hide its
 // latency behind, so the CTA has only 4 warps (row classes), a lane takes
@@ -187,7 +188,8 @@ __device__ __forceinline__ void mueller_acc(float4 &r01, float4 &r23, const floa
 // ... of its warp's rows) and a unit is a whole offset group: a.passes
 // independent updates per visibility and lane.
 template <int ST, int R, int NPOL, int TMAX>
-__global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT), NPOL == 4 ? AW_RG_MINB : 4)
+__global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 3 ? 192 : TMAX == 2 ? 256 : RG_MAXT),
+                                  NPOL == 4 ? AW_RG_MINB : 4)
     grid_region_kernel(RegionArgs a) {
     // row stride of the region in cells: Stokes I pads two cells, so that region
     // rows 4 apart (the row classes of one pass of a half-warp) fall on the other
@@ -404,36 +406,47 @@ __global__ void __launch_bounds__(NPOL == 1 ? 128 : (TMAX == 2 ? 256 : RG_MAXT),
                         __syncthreads();
                     }
                 }
-            } else if constexpr (TMAX == 2) {
-                // two passes of one offset group at a time: both taps' cells are
-                // read before either is written (distinct taps, distinct cells)
+            } else if constexpr (TMAX >= 2) {
+                // TMAX passes of one offset group at a time: all their taps' cells are
+                // read before any is written (distinct taps, distinct cells)
                 for (int g = 0; g < s_ng; ++g) {
-                    for (int p0 = 0; p0 < passes; p0 += 2) {
-                        const bool two = p0 + 1 < passes;
-                        float2 kA[P], kB[P];
+                    for (int p0 = 0; p0 < passes; p0 += TMAX) {
+                        float2 kk[TMAX][P];
+                        int tt[TMAX], ct[TMAX];
 #pragma unroll
-                        for (int m = 0; m < P; ++m) { kA[m] = make_float2(0.f, 0.f); kB[m] = kA[m]; }
-                        load_unit(g * passes + p0, kA);
-                        if (two) load_unit(g * passes + p0 + 1, kB);
-                        int ta, cta, tb = -1, ctb = 0;
-                        tap_of(p0, ta, cta);
-                        if (two) tap_of(p0 + 1, tb, ctb);
+                        for (int i = 0; i < TMAX; ++i) {
+#pragma unroll
+                            for (int m = 0; m < P; ++m) kk[i][m] = make_float2(0.f, 0.f);
+                            tt[i] = -1;
+                            ct[i] = 0;
+                            if (p0 + i < passes) {
+                                load_unit(g * passes + p0 + i, kk[i]);
+                                tap_of(p0 + i, tt[i], ct[i]);
+                            }
+                        }
                         const int sg1 = s_gss[g + 1];
                         for (int sg = s_gss[g]; sg < sg1; ++sg) {
                             const int j1 = s_ss[sg + 1];
                             for (int j = s_ss[sg]; j < j1; ++j) {
                                 const int base = s_cell[j];
-                                const int ca = base + cta, cb = base + ctb;
-                                const bool oa = ta >= 0 && RG_BOK(ca >= 0 && ca < RR, BC_R_SMEM);
-                                const bool ob = tb >= 0 && RG_BOK(cb >= 0 && cb < RR, BC_R_SMEM);
                                 const float4 v01 = s_v[2 * j], v23 = s_v[2 * j + 1];
-                                float4 a01 = z4, a23 = z4, b01 = z4, b23 = z4;
-                                if (oa) { a01 = reg01[ca]; a23 = reg23[ca]; }
-                                if (ob) { b01 = reg01[cb]; b23 = reg23[cb]; }
-                                mueller_acc(a01, a23, kA, v01, v23);
-                                mueller_acc(b01, b23, kB, v01, v23);
-                                if (oa) { reg01[ca] = a01; reg23[ca] = a23; }
-                                if (ob) { reg01[cb] = b01; reg23[cb] = b23; }
+                                float4 c01[TMAX], c23[TMAX];
+                                bool on[TMAX];
+#pragma unroll
+                                for (int i = 0; i < TMAX; ++i) {
+                                    const int c = base + ct[i];
+                                    on[i] = tt[i] >= 0 && RG_BOK(c >= 0 && c < RR, BC_R_SMEM);
+                                    c01[i] = on[i] ? reg01[c] : z4;
+                                    c23[i] = on[i] ? reg23[c] : z4;
+                                }
+#pragma unroll
+                                for (int i = 0; i < TMAX; ++i) mueller_acc(c01[i], c23[i], kk[i], v01, v23);
+#pragma unroll
+                                for (int i = 0; i < TMAX; ++i)
+                                    if (on[i]) {
+                                        reg01[base + ct[i]] = c01[i];
+                                        reg23[base + ct[i]] = c23[i];
+                                    }
                                 // the next visibility's cells may be this one's cells of other lanes
                                 __syncwarp();
                             }
@@ -498,7 +511,8 @@ int launch_region_t(const RegionArgs &a, int BT, int sm_count, cudaStream_t s) {
     if (a.R != AW_RG_RMAX) return aw_set_error(AW_EINVAL, "region side %d", a.R);
     if (NPOL == 1 && (a.passes > TMAX || (BT != 64 && BT != 128)))
         return aw_set_error(AW_EINVAL, "Stokes-I region: %d taps a lane, %d threads", a.passes, BT);
-    if (NPOL == 4 && TMAX == 2 && BT > 256) return aw_set_error(AW_EINVAL, "paired region units: %d threads", BT);
+    if (NPOL == 4 && TMAX >= 2 && BT > (TMAX == 3 ? 192 : 256))
+        return aw_set_error(AW_EINVAL, "grouped region units: %d threads", BT);
     auto kern = grid_region_kernel<ST, AW_RG_RMAX, NPOL, TMAX>;
     const size_t smem = region_smem_bytes(a.R, NPOL);
     AW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -597,7 +611,9 @@ int aw_launch_grid_region(const aw_plan *p, const aw_kernel_set *k, const void *
         a.passes = ((rc.S / a.M) * rc.S + 31) / 32;
         int r;
         const int st = k->spec.storage;
-        if (p->npol == 4 && a.passes >= 2 && rc.BT <= 256) {
+        if (p->npol == 4 && a.passes == 3 && rc.BT <= 192) {
+            r = launch_region4<3>(a, st, rc.BT, sms, s);
+        } else if (p->npol == 4 && a.passes >= 2 && rc.BT <= 256) {
             r = launch_region4<2>(a, st, rc.BT, sms, s);
         } else if (p->npol == 4) {
             r = launch_region4<1>(a, st, rc.BT, sms, s);
