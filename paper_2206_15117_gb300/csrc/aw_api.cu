@@ -254,11 +254,14 @@ int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kse
     p->device = ctx->device;
     aw_tune cached{};
     if (!tune && ctx->has_tune) {
-        // a cached hybrid split names planes of the set it was tuned on: a set
-        // without planes on both sides of it takes the offset schedule instead
+        // a cached split names planes of the set it was tuned on: a hybrid split
+        // without planes of this set on both sides of it takes the offset
+        // schedule instead; a region split past this set's planes (the first
+        // split_planes planes on the region kernel) means all of them
         cached = ctx->tune_cache;
         if (cached.grid_mode == AW_GRID_HYBRID && (cached.split_planes < 1 || cached.split_planes >= kset->spec.nw))
             cached.grid_mode = AW_GRID_OFFSETS;
+        if (cached.grid_mode == AW_GRID_REGION && cached.split_planes > kset->spec.nw) cached.split_planes = 0;
         tune = &cached;
     }
     rc = aw_plan_build(ctx, vis, kset, tune, p, S_(stream));
