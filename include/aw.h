@@ -295,9 +295,8 @@ int aw_kernel_set_destroy(aw_kernel_set *kset);
  * tune == NULL uses the last aw_autotune result of this context (its cache),
  * or tile 32, chunk 256 if the context has none; a cached HYBRID tune whose
  * split_planes is not inside 1..nw-1 of this kernel set is used with the
- * OFFSETS schedule instead, and a cached REGION tune whose split_planes is
- * above this set's nw with split_planes 0 (all planes).  Synchronises
- * `stream`.
+ * OFFSETS schedule instead, as is a cached REGION tune whose split_planes is
+ * above this set's nw.  Synchronises `stream`.
  */
 int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kset,
                    const aw_tune *tune, aw_plan **out, void *stream);

@@ -255,13 +255,14 @@ int aw_plan_create(aw_ctx *ctx, const aw_vis_desc *vis, const aw_kernel_set *kse
     aw_tune cached{};
     if (!tune && ctx->has_tune) {
         // a cached split names planes of the set it was tuned on: a hybrid split
-        // without planes of this set on both sides of it takes the offset
-        // schedule instead; a region split past this set's planes (the first
-        // split_planes planes on the region kernel) means all of them
+        // without planes of this set on both sides of it, or a region split past
+        // this set's planes, takes the offset schedule instead (a set of another
+        // plane layout was not tuned; the offset kernel suits any layout)
         cached = ctx->tune_cache;
         if (cached.grid_mode == AW_GRID_HYBRID && (cached.split_planes < 1 || cached.split_planes >= kset->spec.nw))
             cached.grid_mode = AW_GRID_OFFSETS;
-        if (cached.grid_mode == AW_GRID_REGION && cached.split_planes > kset->spec.nw) cached.split_planes = 0;
+        if (cached.grid_mode == AW_GRID_REGION && cached.split_planes > kset->spec.nw)
+            cached.grid_mode = AW_GRID_OFFSETS;
         tune = &cached;
     }
     rc = aw_plan_build(ctx, vis, kset, tune, p, S_(stream));
