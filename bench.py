@@ -1265,31 +1265,8 @@ def run_ours(args, rank, world, dist):
     dom = ("aw_grid (%s)" % gname) if g_ms >= d_ms else "aw_degrid (degrid_items_kernel)"
     peak_tflops, peak_src = fp32_peak_tflops(dev_index)
     achieved = flops / (dom_ms / 1e3) / 1e12
-    # DRAM bytes per launch of the dominant kernel: the one-bin-pair ncu capture summarised in
-    # profiles/dram_traffic_fullpol_aw_1pair.md (1,139,896 visibilities: region gridding 146.5 MB,
-    # degridding 96.5 MB), scaled to this workload by the visibility count (the per-visibility bytes
-    # scale; the tables touched per visibility grow with the bins, so this is a lower bound).  Only
-    # for the region schedule and the degridder at full size; null otherwise.
-    per_vis = {"region": 146.5e6 / 1139896, "degrid_items_kernel": 96.5e6 / 1139896}
-    # The region capture predates the region kernel's three-pass units (supports
-    # 20 and 24): its counters no longer describe the kernel that runs, so the
-    # region figure is reported beside `traffic` (null), not as it.
-    traffic, traffic_prev = None, None
-    if not args.subset:
-        if g_ms >= d_ms and tune.grid_mode == aw.AW_GRID_REGION:
-            traffic_prev = per_vis["region"] * info.nvalid
-        elif g_ms < d_ms:
-            traffic = per_vis["degrid_items_kernel"] * info.nvalid
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": traffic,
-            "traffic_source": ("profiles/dram_traffic_fullpol_aw_1pair.md, scaled by the visibility count "
-                               "(lower bound)") if traffic else None,
-            "peak_source": peak_src, "flops_per_launch": flops}
-    if traffic_prev:
-        roof["traffic_previous_region_kernel"] = {
-            "bytes": traffic_prev,
-            "source": "profiles/dram_traffic_fullpol_aw_1pair.md (the region kernel with paired passes, before the "
-                      "three-pass units), scaled by the visibility count (lower bound)"}
+    roof = roofline_entry(dom, achieved, peak_tflops, peak_src, flops, g_ms, d_ms,
+                          region=tune.grid_mode == aw.AW_GRID_REGION, nvalid=info.nvalid, subset=args.subset)
     alt = bf16_scaled_peak()
     if alt:
         roof["peak_alt"] = {"value": alt, "frac": achieved / alt,
@@ -1533,6 +1510,38 @@ def hybrid_split(aw, plan, kw, share: float) -> int:
     below = np.concatenate([[0.0], np.cumsum(taps) / max(taps.sum(), 1.0)])   # below[q]: share of planes < q
     q = int(np.argmin(np.abs(below - share)))
     return max(1, min(q, kw["nw"] - 1))
+
+
+# DRAM bytes per visibility of the dominant kernels from the one-bin-pair ncu capture summarised in
+# profiles/dram_traffic_fullpol_aw_1pair.md (1,139,896 visibilities: region gridding 146.5 MB,
+# degridding 96.5 MB); scaled to a workload by its visibility count (the per-visibility bytes scale;
+# the tables touched per visibility grow with the bins, so the figure is a lower bound).
+TRAFFIC_PER_VIS = {"region": 146.5e6 / 1139896, "degrid_items_kernel": 96.5e6 / 1139896}
+
+
+def roofline_entry(kernel, achieved, peak, peak_src, flops, g_ms, d_ms, region, nvalid, subset):
+    """The `roofline` object of the dominant step (gridding if g_ms >= d_ms).  `traffic` is the
+    scaled one-bin-pair capture when it describes the kernel that runs: the degridder; the region
+    capture predates the region kernel's three-pass units (supports 20 and 24), so for the region
+    schedule `traffic` is null and the previous figure stands beside it, labelled.  Null at the
+    subset scale and for the other schedules."""
+    traffic, traffic_prev = None, None
+    if not subset:
+        if g_ms >= d_ms and region:
+            traffic_prev = TRAFFIC_PER_VIS["region"] * nvalid
+        elif g_ms < d_ms:
+            traffic = TRAFFIC_PER_VIS["degrid_items_kernel"] * nvalid
+    roof = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": ("profiles/dram_traffic_fullpol_aw_1pair.md, scaled by the visibility count "
+                               "(lower bound)") if traffic else None,
+            "peak_source": peak_src, "flops_per_launch": flops}
+    if traffic_prev:
+        roof["traffic_previous_region_kernel"] = {
+            "bytes": traffic_prev,
+            "source": "profiles/dram_traffic_fullpol_aw_1pair.md (the region kernel with paired passes, before "
+                      "the three-pass units), scaled by the visibility count (lower bound)"}
+    return roof
 
 
 def fp32_peak_tflops(device_index: int = 0):
